@@ -1,0 +1,173 @@
+"""The offline stage of Algorithm 1 (steps 1.1-1.4) for every subdomain of a
+problem from ``sfm_inputs``, plus helpers shared by the oracle's tests: the
+global and "slit" fine grids and the trace error metric."""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+import sfm_inputs as inputs
+
+from . import fine, faces, rom, sfrac, project, coupled
+
+
+class SubdomainROM:
+    """Everything the oracle computes for one subdomain."""
+
+    def __init__(self, problem, topo, s, keep_basis=False):
+        self.box = problem.sub_box(s)
+        self.K, self.mass = fine.assemble(problem.c, problem.h, self.box)
+        self.B = faces.B_matrix(self.box, topo.mf[s], problem.h)
+        self.F = self.B / np.sqrt(self.mass)[:, None]
+        self.sigma = problem.sigma
+        self.k = int(problem.k_sub[s])
+        solve = rom.shifted_solver(self.K, self.mass, self.sigma)
+        V = rom.krylov_basis(solve, self.F, self.k)
+        L = fine.symmetrised(self.K, self.mass)
+        self.Lt, self.Ft = rom.galerkin(L, V, self.F)
+        self.alpha, self.C, self.R1, Qh = sfrac.block_lanczos(self.Lt, self.Ft, self.k)
+        self.Gamma, self.Gammahat, self.G, self.min_eigs = sfrac.gamma_transform(
+            self.alpha, self.C, self.R1)
+        self._V, self._Qh = V, Qh
+        if keep_basis:
+            self.V, self.Qh, self.L = V, Qh, L
+
+    def rows(self, vec):
+        """Projected rows (k, b) of a nodal vector (Algorithm 1 step 1.4)."""
+        return project.project(self._V, self._Qh, self.G, self.mass, vec)
+
+    def drop_basis(self):
+        self._V = self._Qh = None
+
+
+def build(problem, keep=False, subs=None):
+    """Build the ROM set of ``problem``.  ``keep`` keeps every subdomain's
+    ``SubdomainROM`` (with V) in ``.subroms``; ``subs`` restricts the build
+    to a list of subdomains (their coefficients only, for sampling)."""
+    topo = faces.Topology(problem)
+    gmass = fine.global_mass_ijk(problem)
+    h = problem.h
+    src_w = [inputs.gaussian_node_weights(x, problem.src_width, h, problem.nx, problem.ny,
+                                          problem.nz) for x in problem.src_xyz]
+    rec_w = [inputs.trilinear_node_weights(x, h, problem.nx, problem.ny, problem.nz)
+             for x in problem.rec_xyz]
+    Gam, Gh = [None] * problem.nsub, [None] * problem.nsub
+    src = [dict() for _ in src_w]
+    rec = [dict() for _ in rec_w]
+    kept = {}
+    for s in (range(problem.nsub) if subs is None else subs):
+        sr = SubdomainROM(problem, topo, s, keep_basis=keep)
+        Gam[s] = np.stack(sr.Gamma)
+        Gh[s] = np.stack(sr.Gammahat)
+        for q, (nodes, w) in enumerate(src_w):
+            v = project.local_share(sr.box, gmass, sr.mass, nodes, w)
+            if v is not None:
+                src[q][s] = sr.rows(v)
+        for r, (nodes, w) in enumerate(rec_w):
+            v = project.local_share(sr.box, gmass, sr.mass, nodes, w)
+            if v is not None:
+                rec[r][s] = sr.rows(v)
+        if keep:
+            kept[s] = sr
+        else:
+            sr.drop_basis()
+    if subs is not None:
+        return topo, Gam, Gh, kept
+    rs = coupled.RomSet(topo, Gam, Gh, src, rec)
+    rs.subroms = kept
+    return rs
+
+
+def rom_dt(rs, safety=0.9):
+    """``safety * dt_CFL`` of the coupled ROM system (0.9 by default)."""
+    return safety * coupled.Assembled(rs).cfl_dt()
+
+
+# ----------------------------------------------------------------------------
+# reference fine grids
+# ----------------------------------------------------------------------------
+
+def fine_system(problem):
+    """Global fine grid: ``(K, M, force[N, nshots], rec_rows[nrec, N])``."""
+    K, mass = fine.assemble_global(problem)
+    box = fine.global_box(problem)
+    return (K, mass) + _point_vectors(problem, box, [(box, np.arange(K.shape[0]))], K.shape[0])
+
+
+def _point_vectors(problem, box, pieces, n):
+    h = problem.h
+    gmass = fine.global_mass_ijk(problem)
+    force = np.zeros((n, problem.nshots))
+    R = np.zeros((problem.nrec, n))
+    for q, x in enumerate(problem.src_xyz):
+        nodes, w = inputs.gaussian_node_weights(x, problem.src_width, h, problem.nx,
+                                                problem.ny, problem.nz)
+        for pbox, gidx in pieces:
+            m = fine.lumped_mass(problem.c, h, pbox)
+            v = project.local_share(pbox, gmass, m, nodes, w)
+            if v is not None:
+                np.add.at(force[:, q], gidx, v)
+    for r, x in enumerate(problem.rec_xyz):
+        nodes, w = inputs.trilinear_node_weights(x, h, problem.nx, problem.ny, problem.nz)
+        for pbox, gidx in pieces:
+            m = fine.lumped_mass(problem.c, h, pbox)
+            v = project.local_share(pbox, gmass, m, nodes, w)
+            if v is not None:
+                np.add.at(R[r], gidx, v)
+    return force, sp.csr_matrix(R)
+
+
+def slit_system(problem):
+    """The fine grid the ROM converges to under the open-face reading: the
+    subdomain operators ``K^a, M^a`` assembled with only the OPEN-face nodes
+    of shared faces identified; subdomain edge and corner nodes keep one copy
+    per subdomain.  Returns ``(K, M, force, rec_rows)``."""
+    topo = faces.Topology(problem)
+    gid_of = {}
+    pieces = []
+    nxt = 0
+    Ks, Ms = [], []
+    for s in range(problem.nsub):
+        box = problem.sub_box(s)
+        K, m = fine.assemble(problem.c, problem.h, box)
+        gidx = -np.ones(K.shape[0], dtype=int)
+        for f in range(6):
+            if topo.nbr[s, f] < 0:
+                continue
+            idx, _, _, _ = faces.open_face_nodes(box, f)
+            ii, jj, kk = fine.node_coords(box)
+            for li in idx:
+                key = (ii[li], jj[li], kk[li])
+                if key not in gid_of:
+                    gid_of[key] = nxt
+                    nxt += 1
+                gidx[li] = gid_of[key]
+        free = gidx < 0
+        gidx[free] = nxt + np.arange(free.sum())
+        nxt += int(free.sum())
+        pieces.append((box, gidx))
+        Ks.append(K)
+        Ms.append(m)
+    n = nxt
+    Kg = sp.csr_matrix((n, n))
+    Mg = np.zeros(n)
+    for (box, gidx), K, m in zip(pieces, Ks, Ms):
+        P = sp.csr_matrix((np.ones(len(gidx)), (gidx, np.arange(len(gidx)))), shape=(n, len(gidx)))
+        Kg = Kg + P @ K @ P.T
+        np.add.at(Mg, gidx, m)
+    return (Kg.tocsr(), Mg) + _point_vectors(problem, None, pieces, n)
+
+
+def fine_traces(system, dt, nsteps, wavelet):
+    """Fine-grid leapfrog traces ``[nshots, nrec, nsteps+1]`` of a system from
+    :func:`fine_system` / :func:`slit_system`."""
+    K, mass, force, R = system
+    wavelet = np.asarray(wavelet).reshape(force.shape[1], -1)
+    return np.stack([fine.leapfrog(K, mass, dt, nsteps, force[:, q], wavelet[q], R)
+                     for q in range(force.shape[1])])
+
+
+def rel_l2(d, ref):
+    """Relative L2 error over all receivers and samples concatenated."""
+    d, ref = np.asarray(d, np.float64), np.asarray(ref, np.float64)
+    return float(np.linalg.norm(d - ref) / np.linalg.norm(ref))
