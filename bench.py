@@ -1,0 +1,405 @@
+#!/usr/bin/env python3
+"""Throughput of the online stage (Algorithm 1 stage 2) on one GB300.
+
+Workload: the 192^3-cell model in 8x8x8 = 512 subdomains of 24^3 cells,
+m = 8 modes per face (b = 48), k = 16 levels, one 20 Hz Ricker shot, 1024
+surface receivers, 4000 leapfrog steps (seeded synthetic layered model with a
+Gaussian lens; ``sfm_inputs.config2``).  One bench step is one pass of the
+whole online stage: ``sfm_run`` over the 4000 time steps.
+
+Metric: equivalent fine-grid cell-steps/s per shot,
+N_cells * nsteps * (dt / dt_fine) * nshots / seconds, for the fastest
+precision whose traces stay within 1e-3 (relative L2) of the FP64 run of the
+same ROMs.  dt is 0.9x the ROM leapfrog limit (power iteration on the GPU),
+dt_fine 0.9x the fine grid's limit from the Gershgorin bound of its operator.
+
+The offline ROM build (GPU, FP64), the source/receiver projection and the
+CFL estimate happen before timing.  ``--impl reference`` times the FP64 CPU
+oracle (``oracle/``) instead; ``cpu_baseline`` in the default line is the same
+oracle timed on a bounded sample."""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import sfm_inputs as inputs  # noqa: E402
+
+METRIC = "equivalent fine-grid cell-steps/s per shot at <=1e-3 trace error vs FP64"
+UNIT = "cell-steps/s"
+GATE = 1e-3
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="sfm", choices=["sfm", "reference"])
+    ap.add_argument("--nsteps", type=int, default=None, help="time steps per run (default: 4000)")
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "fp32x2", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-steps", type=int, default=60)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# metric helpers (no method arithmetic)
+
+def fine_dt(p, safety=0.9):
+    """0.9 x 2/sqrt(lambda) with lambda the Gershgorin bound of the fine
+    operator M^{-1} K (vertex-centred cells: conductance h/4 per edge per
+    cell, lumped mass h^3/(8c^2) per corner): every node's row sum times two
+    over its mass."""
+    h = p.h
+    inv = h ** 3 / (8.0 * p.c ** 2)
+    m = np.zeros((p.nz + 1, p.ny + 1, p.nx + 1))
+    g = np.zeros_like(m)
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                m[dz:dz + p.nz, dy:dy + p.ny, dx:dx + p.nx] += inv
+                g[dz:dz + p.nz, dy:dy + p.ny, dx:dx + p.nx] += 3 * h / 4.0   # 3 edges per corner
+    lam = float(np.max(2.0 * g / m))
+    return safety * 2.0 / np.sqrt(lam)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.f.flush()
+
+    def summary(self):
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nme, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nme)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": FALLBACK_HBM}, "fallback"
+
+
+def algorithmic_bytes_per_step(nsub, b, k, m, nrpairs, word):
+    """Bytes one time step must move for one shot (the per-unit figure of the
+    roofline): packed symmetric Gamma_1..k and Gammahat_2..k, U and delta read
+    and written, the face blocks H_f, the face data written and read back,
+    and the receiver rows; ``word`` bytes per number."""
+    coef = nsub * (2 * k - 1) * b * (b + 1) // 2
+    state = nsub * 4 * k * b
+    faces = nsub * 6 * m * (m + 1) // 2
+    mail = nsub * 2 * b
+    rec = nrpairs * k * b
+    return (coef + state + faces + mail + rec) * word
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (cpu_baseline and --impl reference)
+
+def oracle_sample(nsteps_sample):
+    """The config-2 stepping workload (same geometry, b, k, receivers) with
+    ROM coefficients the oracle builds for a uniform 3000 m/s medium on the
+    same grid (one distinct subdomain build): the cost of the stepping does
+    not depend on the coefficients' values."""
+    from oracle import pipeline
+    p = inputs.config2()
+    p.c = np.full_like(p.c, 3000.0)
+    rs = pipeline.build(p)
+    dt = pipeline.rom_dt(rs)
+    return p, rs, dt, fine_dt(p)
+
+
+def time_oracle(p, rs, dt, dtf, nsteps_sample):
+    from oracle import coupled
+    w = inputs.wavelet_samples(p, dt, nsteps_sample)
+    t0, c0 = time.perf_counter(), time.process_time()
+    coupled.step_structured(rs, dt, nsteps_sample, w)
+    wall = time.perf_counter() - t0
+    cpu = time.process_time() - c0
+    ncell = p.nx * p.ny * p.nz
+    value = ncell * nsteps_sample * (dt / dtf) * rs.nshots / wall
+    return value, wall, max(1, round(cpu / wall))
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    p, rs, dt, dtf = oracle_sample(args.cpu_sample_steps)
+    ns = args.cpu_sample_steps
+    for _ in range(args.warmup):
+        time_oracle(p, rs, dt, dtf, ns)
+    vals, walls, cores = [], [], 1
+    for _ in range(args.steps):
+        v, wall, cores = time_oracle(p, rs, dt, dtf, ns)
+        vals.append(v)
+        walls.append(wall)
+    value = statistics.mean(vals)
+    sample = (f"config-2 stepping (512 subdomains, b=48, k=16, 1024 receivers, 1 shot), "
+              f"{ns} of its time steps per bench step, oracle-built ROMs of a uniform "
+              f"3000 m/s medium on the same grid")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(walls),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": p.name, "sample_time_steps": ns},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1406_6923_gb300 import sfm
+
+    p = inputs.config2()
+    nsteps = args.nsteps or p.nsteps
+    stream = torch.cuda.current_stream()
+    h = sfm.sfm_create(local)
+    sfm.sfm_set_stream(h, stream.cuda_stream)
+    t0 = time.perf_counter()
+    sfm.sfm_set_model(h, p.c, p.h, p.xcuts, p.ycuts, p.zcuts)
+    rep = sfm.sfm_build_roms(h, p.m_sub, p.k_sub, p.sigma)
+    sfm.sfm_project_sources(h, p.src_xyz, p.src_width)
+    sfm.sfm_project_receivers(h, p.rec_xyz)
+    lam, dtc = sfm.sfm_cfl_dt(h, 1000)
+    build_s = time.perf_counter() - t0
+    dt = p.dt_safety * dtc
+    dtf = fine_dt(p)
+    nshots, nrec = p.nshots, p.nrec
+    wav = torch.tensor(inputs.wavelet_samples(p, dt, nsteps), dtype=torch.float64, device="cuda")
+    tr = torch.empty((nshots, nrec, nsteps + 1), dtype=torch.float64, device="cuda")
+
+    def run(prec):
+        _, ms = sfm.sfm_run(h, prec, dt, nsteps, None, nshots, nrec,
+                            device_ptrs=(wav.data_ptr(), tr.data_ptr()))
+        return ms
+
+    # FP64 reference of the same ROMs, then the precision gate
+    run(sfm.SFM_FP64)
+    torch.cuda.synchronize()
+    ref = tr.cpu().numpy()
+    modes = {"fp32": sfm.SFM_FP32, "fp32x2": sfm.SFM_FP32X2, "fp64": sfm.SFM_FP64}
+    errors = {"fp64": 0.0}
+    for name in ("fp32", "fp32x2"):
+        try:
+            run(modes[name])
+            torch.cuda.synchronize()
+            errors[name] = rel_l2(tr.cpu().numpy(), ref)
+        except sfm.SfmError as e:
+            errors[name] = float("inf") if e.code == sfm.SFM_ERR_UNSTABLE else None
+    if args.precision == "auto":
+        chosen = next(n for n in ("fp32", "fp32x2", "fp64")
+                      if errors.get(n) is not None and errors[n] <= GATE)
+    else:
+        chosen = args.precision
+    prec = modes[chosen]
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    for _ in range(args.warmup):
+        run(prec)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    kern_ms = []
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            kern_ms.append(run(prec))
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    launches = sfm.sfm_last_launches(h) * args.steps
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = statistics.mean(step_ms)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ncell = p.nx * p.ny * p.nz
+    per_rank = ncell * nsteps * (dt / dtf) * nshots / (ms * 1e-3)
+    value = per_rank * world
+
+    # end to end through the public API with host buffers (H2D of the
+    # wavelet and D2H of the traces inside the timed region)
+    host_w = inputs.wavelet_samples(p, dt, nsteps)
+    host_tr = np.empty((nshots, nrec, nsteps + 1))
+    e2e_t = []
+    for i in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        sfm.sfm_run(h, prec, dt, nsteps, host_w, nshots, nrec, traces=host_tr)
+        e2e_t.append(time.perf_counter() - t1)
+    e2e_val = ncell * nsteps * (dt / dtf) * nshots / statistics.mean(e2e_t) * world
+
+    # roofline of the persistent stepping kernel
+    pk, pk_kind = peaks()
+    word = {"fp32": 4, "fp32x2": 8, "fp64": 8}[chosen]
+    nrpairs = int(getattr(h, "nrpairs", 0) or 0)
+    bytes_step = algorithmic_bytes_per_step(p.nsub, 48, 16, 8, count_rpairs(sfm, h, p), word)
+    kms = statistics.mean(kern_ms)
+    achieved = bytes_step * nsteps / (kms * 1e-3) / 1e9
+    traffic = read_traffic()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
+            "peak_source": f"{pk_kind} HBM copy", "kernel": "step_kernel",
+            "kernel_ms": kms, "bytes_per_time_step": bytes_step}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        po, rs, dto, dtfo = oracle_sample(args.cpu_sample_steps)
+        v, wall_c, cores = time_oracle(po, rs, dto, dtfo, args.cpu_sample_steps)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": (f"config-2 stepping, {args.cpu_sample_steps} of its time steps, "
+                          f"oracle-built ROMs of a uniform 3000 m/s medium on the same grid, "
+                          f"{wall_c:.1f} s")}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": {"fp32": "f32", "fp32x2": "f32x2", "fp64": "f64"}[chosen],
+           "data": "synthetic",
+           "config": {"workload": p.name, "cells": ncell, "subdomains": p.nsub, "b": 48, "k": 16,
+                      "shots": nshots, "receivers": nrec, "time_steps": nsteps,
+                      "precision": chosen, "trace_err_vs_fp64": errors,
+                      "dt": dt, "dt_fine": dtf, "dt_ratio": dt / dtf,
+                      "conservative_value": ncell * nsteps * nshots / (ms * 1e-3) * world,
+                      "l2": "256 MB buffer written between timed iterations",
+                      "parallelism": "replicas" if world > 1 else "single GPU",
+                      "offline_build_s": build_s, "build": rep},
+           "roofline": roof, "cpu_baseline": cpu,
+           "e2e": {"value": e2e_val, "unit": UNIT,
+                   "h2d_bytes_per_step": int(host_w.nbytes), "d2h_bytes_per_step": int(host_tr.nbytes)},
+           "gpu_launches": launches, "clocks": clk.summary(), "wall_s_timed": wall}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    sfm.sfm_destroy(h)
+    if dist:
+        dist.destroy_process_group()
+
+
+def count_rpairs(sfm, h, p):
+    """Receiver (receiver, subdomain) pairs of the workload: a receiver on a
+    node shared by several subdomains has one pair per subdomain."""
+    xs = [np.asarray(p.xcuts), np.asarray(p.ycuts), np.asarray(p.zcuts)]
+    n = 0
+    for x in p.rec_xyz:
+        nodes, w = inputs.trilinear_node_weights(x, p.h, p.nx, p.ny, p.nz)
+        subs = set()
+        for nd in nodes:
+            cand = [np.nonzero((c[:-1] <= nd[a]) & (nd[a] <= c[1:]))[0] for a, c in enumerate(xs)]
+            for i in cand[0]:
+                for j in cand[1]:
+                    for k in cand[2]:
+                        subs.add((i, j, k))
+        n += len(subs)
+    return n
+
+
+def read_traffic():
+    """DRAM bytes per launch of the stepping kernel from the committed ncu
+    summary, when it was taken on the current kernel source (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "step_kernel_config2.md")
+    src = b""
+    for f in ("step.cu", "numeric.cuh"):
+        with open(os.path.join(ROOT, "paper_1406_6923_gb300", "csrc", f), "rb") as fh:
+            src += fh.read()
+    digest = hashlib.sha256(src).hexdigest()[:16]
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in txt.splitlines():
+        if ":" in line and line.strip().startswith("- traffic"):
+            k, v = line.split(":", 1)
+            vals[k.strip("- ").strip()] = v.strip()
+    if vals.get("traffic_source_hash") != digest:
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+if __name__ == "__main__":
+    main()

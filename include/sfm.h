@@ -1,0 +1,234 @@
+/*
+ * libsfm - S-fraction multiscale finite-volume wave propagation on one GPU.
+ *
+ * C ABI of the GB300 (sm_103a) library.  The method is Druskin, Mamonov and
+ * Zaslavsky, "S-fraction multiscale finite-volume method for spectrally
+ * accurate wave propagation": the domain is split into box subdomains, each
+ * subdomain's fine-grid operator is reduced offline to a reduced-order model
+ * (ROM) in matrix S-fraction form (Algorithm 1 stage 1, Eqs. 5-13), and the
+ * ROMs are stepped together with explicit leapfrog, coupled through the
+ * m-dimensional face data of shared subdomain faces at every step
+ * (Algorithm 1 stage 2, Eqs. 17-19).
+ *
+ * Conventions used by every call
+ * -------------------------------
+ *  - Every call returns an int status: SFM_OK (0) or a negative SFM_ERR_*.
+ *    sfm_last_error() describes the last failure on a handle.
+ *  - A handle owns all device memory it allocates; nothing is shared
+ *    between handles.  Calls on one handle must not run concurrently.
+ *  - Array arguments are host memory, row-major, owned by the caller, and
+ *    read or written only during the call (never retained), unless the call
+ *    says otherwise.
+ *  - Subdomains are numbered 0..nsub-1.  Faces of a subdomain are numbered
+ *    0..5 = -x, +x, -y, +y, -z, +z.  A subdomain's block width is
+ *    b = sum over its 6 faces of the face mode counts m_f; its state has k
+ *    levels U_1..U_k, each in R^b; level 1 is split into the 6 face blocks
+ *    in face order.
+ *  - Sign convention: with the paper's u_tt = A u (A <= 0) we use L = -A;
+ *    all S-fraction coefficients are symmetric positive (semi)definite.
+ */
+#ifndef SFM_H
+#define SFM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sfm_handle sfm_handle;
+
+enum sfm_status {
+    SFM_OK = 0,
+    SFM_ERR_ARG = -1,        /* invalid argument or size                      */
+    SFM_ERR_CUDA = -2,       /* a CUDA runtime call failed                    */
+    SFM_ERR_NOT_SPD = -3,    /* a coefficient block is not positive definite  */
+    SFM_ERR_BREAKDOWN = -4,  /* rank-deficient block in the block Krylov step */
+    SFM_ERR_UNSTABLE = -5,   /* non-finite traces (time step above the CFL)   */
+    SFM_ERR_TIMEOUT = -6,    /* a device-wide barrier timed out               */
+    SFM_ERR_NOMEM = -7,      /* device allocation failed                      */
+    SFM_ERR_STATE = -8       /* call made before the data it needs was set    */
+};
+
+enum sfm_precision {
+    SFM_FP64 = 0,            /* FP64 coefficients, state and sums              */
+    SFM_FP32 = 1,            /* FP32 coefficients, state and sums              */
+    SFM_FP32X2 = 2           /* two-float numbers (hi + lo FP32, ~48-bit
+                                significand) with compensated FP32 arithmetic */
+};
+
+/* flags for sfm_run */
+#define SFM_DEVICE_PTR 1     /* wavelet/traces are device pointers            */
+
+/* Create a handle bound to CUDA device `device`.  *h receives the handle.
+ * Errors: SFM_ERR_ARG (h NULL, bad device), SFM_ERR_CUDA. */
+int sfm_create(sfm_handle** h, int device);
+
+/* Free the handle and all device memory it owns.  NULL is accepted. */
+int sfm_destroy(sfm_handle* h);
+
+/* Static text describing the last error on h (or a global error when h is
+ * NULL).  Valid until the next call on the same handle. */
+const char* sfm_last_error(const sfm_handle* h);
+
+/* Make every later call on h enqueue its work on `stream` (a cudaStream_t
+ * of h's device, owned by the caller and never destroyed by the library);
+ * NULL goes back to a stream the handle owns.  Waits for the handle's
+ * previous stream first. */
+int sfm_set_stream(sfm_handle* h, void* stream);
+
+/*
+ * Subdomain topology (the split of section "Introduction" and the faces
+ * B^{ab} of section "Stage 1").
+ *   nsub          number of subdomains
+ *   k_sub[nsub]   number of S-fraction levels k of each subdomain (>= 1)
+ *   m_face[nsub*6] modes on each face of each subdomain (>= 0); both sides
+ *                 of a shared face must give the same count
+ *   nbr[nsub*6]   neighbour across each face, -1 for an outer face
+ *                 (homogeneous Neumann); must be symmetric: if nbr[s][f] = t
+ *                 then nbr[t][f^1] = s.
+ * Resets coefficients, sources and receivers.
+ * Errors: SFM_ERR_ARG for inconsistent topology.
+ */
+int sfm_set_topology(sfm_handle* h, int nsub, const int* k_sub, const int* m_face,
+                     const int* nbr);
+
+/*
+ * S-fraction coefficients Gamma_j and Gammahat_j, j = 1..k (Eq. 13; used by
+ * Eqs. 12, 18, 19).  For each subdomain s in order: k_s blocks Gamma_1..
+ * Gamma_k, then k_s blocks Gammahat_1..Gammahat_k, each b_s x b_s row-major
+ * FP64 (symmetric).  `count` is the total number of doubles.  Gammahat_1
+ * must be block diagonal over the faces (its face blocks define the face
+ * coupling H_f = (sum over the sides of a face of [Gammahat_1]_f^{-1})^{-1}
+ * of Eq. 18, computed on the device in FP64).
+ * Errors: SFM_ERR_ARG (count mismatch), SFM_ERR_STATE (no topology),
+ * SFM_ERR_NOT_SPD (a face block of Gammahat_1 failed its Cholesky).
+ */
+int sfm_set_coeffs(sfm_handle* h, const double* coeffs, size_t count);
+
+/* Copy the FP64 coefficients currently held (same layout as sfm_set_coeffs)
+ * into `coeffs` (capacity `count` doubles); *needed receives the size. */
+int sfm_get_coeffs(sfm_handle* h, double* coeffs, size_t count, size_t* needed);
+
+/*
+ * Projected point sources (Algorithm 1 step 1.4 / Eq. 16): the force of shot
+ * q acts on level j of subdomain s as Gammahat_j p_j f_q(t).  Given as
+ * npairs (shot, subdomain) pairs; pair i has rows[off_i .. off_i + k_s*b_s)
+ * (levels 1..k, each b_s long), with off_i the running sum of the previous
+ * pairs' k*b.  A (shot, subdomain) pair may appear at most once.
+ */
+int sfm_set_sources(sfm_handle* h, int nshots, int npairs, const int* pair_shot,
+                    const int* pair_sub, const double* rows);
+
+/*
+ * Projected receivers: receiver r reads d_r = sum over its pairs of
+ * sum_j rho_j^T U_j (Eq. 16 inverted).  Layout as sfm_set_sources.
+ */
+int sfm_set_receivers(sfm_handle* h, int nrec, int npairs, const int* pair_rec,
+                      const int* pair_sub, const double* rows);
+
+/*
+ * Coupled leapfrog time stepping (Algorithm 1 stage 2): from rest, for
+ * n = 0..nsteps-1 the right-hand sides of Eqs. 18-19 (with the source term
+ * f_q(t_n)) are evaluated at t_n = n*dt and
+ *     delta^{n+1} = delta^n + dt^2 a^n,  U^{n+1} = U^n + delta^{n+1}.
+ *   precision      SFM_FP64, SFM_FP32 or SFM_FP32X2 (coefficients, state, sums)
+ *   wavelet        [nshots][nsteps] FP64 samples f_q(t_n)
+ *   traces         [nshots][nrec][nsteps+1] FP64 output, d_r(t_n), n=0..nsteps
+ *   flags          SFM_DEVICE_PTR: wavelet and traces are device pointers
+ *   kernel_ms      if not NULL, receives the device time of the persistent
+ *                  stepping kernel alone (CUDA events around its launch)
+ * All shots are stepped in one launch.  One persistent cooperative kernel
+ * runs every step; the only cross-block dependency per step is one
+ * device-wide barrier between the face-data publication (step 2.1, with
+ * 2.2) and the face update (step 2.3).
+ * Errors: SFM_ERR_STATE (missing data), SFM_ERR_TIMEOUT (barrier timed out),
+ * SFM_ERR_UNSTABLE (non-finite traces), SFM_ERR_CUDA.
+ */
+int sfm_run(sfm_handle* h, int precision, double dt, int nsteps, const double* wavelet,
+            double* traces, int flags, double* kernel_ms);
+
+/*
+ * Largest eigenvalue of the coupled ROM system's MM^{-1} KK (power
+ * iteration with the FP64 stepping operator, `iters` iterations) and the
+ * leapfrog limit dt_cfl = 2/sqrt(lambda_max).  Either output may be NULL.
+ */
+int sfm_cfl_dt(sfm_handle* h, int iters, double* lambda_max, double* dt_cfl);
+
+/*
+ * ---------------------------------------------------------------------------
+ * Offline stage on the GPU (Algorithm 1 stage 1, FP64)
+ * ---------------------------------------------------------------------------
+ * Fine operator (the paper leaves it generic, Eq. 1; this library reads it
+ * as vertex-centred finite volumes for u_tt = c^2 Laplacian u): each cell of
+ * side h adds h/4 to the conductance of its 12 edges and h^3/(8 c^2) to the
+ * lumped mass of its 8 corners; subdomain boundaries are natural (Neumann).
+ * Face basis (section "Stage 1"): m cosine modes per face on the OPEN face
+ * (face nodes on no subdomain edge, so different faces never overlap),
+ * cos(pi p (s-1/2)/n_s) cos(pi q (t-1/2)/n_t) times h^2, modes by ascending
+ * p^2+q^2, then q, then p; a shared face carries min(m_a, m_b) modes.
+ */
+
+/* Velocity model c[nz][ny][nx] (m/s, cell-centred, FP64) on cells of side
+ * hgrid and the subdomain cuts per axis (node indices, cuts[0] = 0,
+ * cuts[n] = n, at least 2 cells per subdomain).  Subdomain (ix,iy,iz) is
+ * numbered ix + ncx*(iy + ncy*iz).  Errors: SFM_ERR_ARG. */
+int sfm_set_model(sfm_handle* h, int nx, int ny, int nz, double hgrid, const double* c,
+                  int ncx, const int* xcuts, int ncy, const int* ycuts, int ncz,
+                  const int* zcuts);
+
+typedef struct sfm_build_report {
+    double seconds;            /* wall time of the build                        */
+    int cg_iterations_max;     /* most CG iterations of one block solve          */
+    double cg_residual_max;    /* worst final relative residual of the solves    */
+    double krylov_min_ratio;   /* smallest min/max diag of a Krylov block's R    */
+    int nclasses;              /* subdomain shape classes built as batches       */
+} sfm_build_report;
+
+/*
+ * Build every subdomain's ROM and its S-fraction coefficients (Alg. 1 steps
+ * 1.1-1.3): V = orth[F, (L+sigma)^{-1}F, ..., (L+sigma)^{-(k-1)}F] (the
+ * rational block Krylov space of Eq. 6 with one repeated shift sigma > 0 and
+ * F itself as the first block, each solve a Jacobi-preconditioned CG to the
+ * relative residual cg_tol, block Gram-Schmidt twice), L~ = V^T L V,
+ * F~ = V^T F (Eq. 5), block Lanczos on (L~, F~) with full
+ * reorthogonalisation (Eq. 8) and the recursion of Eq. 13.  Sets the
+ * topology and coefficients exactly as sfm_set_topology + sfm_set_coeffs
+ * would.  m_sub[nsub], k_sub[nsub]: modes per face and levels per subdomain.
+ * Errors: SFM_ERR_STATE (no model), SFM_ERR_ARG (block width above 64 or
+ * more modes than open-face nodes), SFM_ERR_BREAKDOWN (a rank-deficient
+ * block or a CG that did not converge), SFM_ERR_NOT_SPD, SFM_ERR_NOMEM.
+ */
+int sfm_build_roms(sfm_handle* h, const int* m_sub, const int* k_sub, double sigma,
+                   double cg_tol, sfm_build_report* rep);
+
+/* Algorithm 1 step 1.4 for point forces: a normalised Gaussian of the given
+ * width (cut at 3 widths) around each point xyz[nshots][3] (metres); a node
+ * shared by several subdomains gives each the share M^a/M of its force.
+ * Projects with the bases of the last sfm_build_roms and sets the sources as
+ * sfm_set_sources would.  Errors: SFM_ERR_STATE (nothing built). */
+int sfm_project_sources(sfm_handle* h, int nshots, const double* xyz, double width);
+
+/* Receivers reading the trilinear interpolation of nodal u at xyz[nrec][3],
+ * the value at a shared node being the mass-weighted mean over its copies.
+ * Sets the receivers as sfm_set_receivers would. */
+int sfm_project_receivers(sfm_handle* h, int nrec, const double* xyz);
+
+/* Number of device kernels launched by the last sfm_run. */
+int sfm_last_launches(const sfm_handle* h, int* launches);
+
+/*
+ * Test hooks for the failure-detection paths (no fault, every wait bounded):
+ *   key 1: device-wide barrier time limit in nanoseconds (default 2e9);
+ *   key 2: index of a block that skips its barrier arrivals (-1 = none), so
+ *          that every block's bounded wait runs out and sfm_run returns
+ *          SFM_ERR_TIMEOUT with the context still usable.
+ * Errors: SFM_ERR_ARG for an unknown key.
+ */
+int sfm_debug_set(sfm_handle* h, int key, long long value);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SFM_H */

@@ -95,64 +95,112 @@ def step_structured(rs, dt, nsteps, wavelet):
     """Coupled leapfrog of all subdomain ROMs (Algorithm 1 stage 2).
 
     ``wavelet``: [nshots, nsteps] samples ``f(t_n)``.  Returns traces
-    ``[nshots, nrec, nsteps+1]`` (float64)."""
+    ``[nshots, nrec, nsteps+1]`` (float64).  The state is one flat array:
+    the face blocks first, then the levels 2..k of every subdomain, grouped
+    by (b, k) so each group's levels are a (S, k-1, b, shots) view."""
     topo = rs.topo
     nsh = rs.nshots
     wavelet = np.asarray(wavelet, dtype=np.float64).reshape(nsh, -1)
     nfm = int(topo.face_off[-1])
-    Uf = np.zeros((nfm, nsh))
-    dUf = np.zeros((nfm, nsh))
-    Hblk = sp.block_diag([sp.csr_matrix(x) for x in rs.H], format="csr")
     groups = []
-    for subs, b, k in _groups(rs):
-        G = np.stack([rs.Gamma[s] for s in subs])
-        Gh = np.stack([rs.Gammahat[s] for s in subs])
-        idx1 = np.stack([topo.level1_index(s) for s in subs])
-        P = np.zeros((len(subs), k, b, nsh))
-        for q in range(nsh):
-            for i, s in enumerate(subs):
-                if s in rs.src[q]:
-                    P[i, :, :, q] = rs.src[q][s]
-        Rr = []
-        for r in range(rs.nrec):
-            row = np.zeros((len(subs), k, b))
-            for i, s in enumerate(subs):
-                if s in rs.rec[r]:
-                    row[i] = rs.rec[r][s]
-            Rr.append(row)
-        groups.append(dict(subs=subs, b=b, k=k, G=G, Gh=Gh, idx1=idx1, P=P,
-                           R=np.stack(Rr) if Rr else np.zeros((0, len(subs), k, b)),
-                           U=np.zeros((len(subs), k - 1, b, nsh)),
-                           dU=np.zeros((len(subs), k - 1, b, nsh))))
+    pos = nfm
+    where = {}                                  # subdomain -> (group, index in group)
+    for gi, (subs, b, k) in enumerate(_groups(rs)):
+        n = len(subs) * (k - 1) * b
+        groups.append(dict(subs=subs, b=b, k=k, lo=pos, hi=pos + n,
+                           G=np.stack([rs.Gamma[s] for s in subs]),
+                           Gh=np.stack([rs.Gammahat[s][1:] for s in subs]),
+                           idx1=np.stack([topo.level1_index(s) for s in subs]),
+                           P=np.zeros((len(subs), k, b, nsh))))
+        for i, s in enumerate(subs):
+            where[s] = (gi, i)
+        pos += n
+    ndof = pos
+    for q in range(nsh):
+        for s, row in rs.src[q].items():
+            gi, i = where[s]
+            groups[gi]["P"][i, :, :, q] = row
+    # sparse receiver matrix over the flat state
+    rr, cc, vv = [], [], []
+    for r in range(rs.nrec):
+        for s, row in rs.rec[r].items():
+            g = groups[where[s][0]]
+            i, b, k = where[s][1], g["b"], g["k"]
+            cols = np.concatenate([g["idx1"][i],
+                                   g["lo"] + i * (k - 1) * b + np.arange((k - 1) * b)])
+            rr.append(np.full(k * b, r))
+            cc.append(cols)
+            vv.append(row.ravel())
+    R = sp.csr_matrix((np.concatenate(vv) if vv else [], (np.concatenate(rr) if rr else [],
+                       np.concatenate(cc) if cc else [])), shape=(rs.nrec, ndof))
+    X = np.zeros((ndof, nsh))                   # U
+    dX = np.zeros((ndof, nsh))                  # delta
+    Hblk = sp.block_diag([sp.csr_matrix(x) for x in rs.H], format="csr")
     out = np.zeros((nsh, rs.nrec, nsteps + 1))
-
-    def readout(it):
-        for g in groups:
-            U = np.concatenate([Uf[g["idx1"]][:, None], g["U"]], axis=1)
-            out[:, :, it] += np.einsum("rskb,skbq->qr", g["R"], U)
-
     for it in range(nsteps):
-        readout(it)
+        out[:, :, it] = (R @ X).T
         w = wavelet[:, it]
+        Uf = X[:nfm]
         face_sum = np.zeros((nfm, nsh))
         for g in groups:
-            U = np.concatenate([Uf[g["idx1"]][:, None], g["U"]], axis=1)     # (S,k,b,q)
+            S, b, k = len(g["subs"]), g["b"], g["k"]
+            Ui = X[g["lo"]:g["hi"]].reshape(S, k - 1, b, nsh)
+            U = np.concatenate([Uf[g["idx1"]][:, None], Ui], axis=1)          # (S,k,b,q)
             Up = np.concatenate([U, np.zeros_like(U[:, :1])], axis=1)
-            delta = Up[:, 1:] - Up[:, :-1]                                   # U_{j+1}-U_j
-            phi = np.einsum("sjab,sjbq->sjaq", g["G"], delta)
+            delta = Up[:, 1:] - Up[:, :-1]                                    # U_{j+1}-U_j
+            phi = np.matmul(g["G"], delta)                                    # Eq. (12)
             src = g["P"] * w
             # (2.1) face data [phi_1 + p_1 f]_f, summed over both sides of a face
             np.add.at(face_sum, g["idx1"], phi[:, 0] + src[:, 0])
             # (2.2) interior levels, Eq. (19)
-            psi = phi[:, 1:] - phi[:, :-1] + src[:, 1:]
-            a = np.einsum("sjab,sjbq->sjaq", g["Gh"][:, 1:], psi)
-            g["dU"] += dt * dt * a
-            g["U"] += g["dU"]
+            a = np.matmul(g["Gh"], phi[:, 1:] - phi[:, :-1] + src[:, 1:])
+            dX[g["lo"]:g["hi"]] += dt * dt * a.reshape(-1, nsh)
         # (2.3) faces, Eq. (18)
-        dUf += dt * dt * (Hblk @ face_sum)
-        Uf += dUf
-    readout(nsteps)
+        dX[:nfm] += dt * dt * (Hblk @ face_sum)
+        X += dX
+    out[:, :, nsteps] = (R @ X).T
     return out
+
+
+def lambda_max(rs, tol=1e-10):
+    """Largest eigenvalue of ``MM^{-1} KK`` without assembling KK: Lanczos
+    (ARPACK) on the symmetric ``C^T KK C``, ``C C^T = MM^{-1}`` blockwise, with
+    ``KK x`` evaluated subdomain by subdomain as ``E^T D^T Gamma D E x``."""
+    topo = rs.topo
+    nfm = int(topo.face_off[-1])
+    int_off = np.zeros(rs.nsub + 1, dtype=int)
+    int_off[0] = nfm
+    for s in range(rs.nsub):
+        int_off[s + 1] = int_off[s] + (rs.k[s] - 1) * rs.b[s]
+    n = int(int_off[-1])
+
+    def sqrt_psd(m):
+        w, U = np.linalg.eigh(0.5 * (m + m.T))
+        return U * np.sqrt(np.maximum(w, 0.0))
+    cs = [sqrt_psd(H) for H in rs.H]
+    for s in range(rs.nsub):
+        cs += [sqrt_psd(rs.Gammahat[s][j]) for j in range(1, rs.k[s])]
+    C = sp.block_diag([sp.csr_matrix(x) for x in cs], format="csr")
+    groups = []
+    for subs, b, k in _groups(rs):
+        E = np.stack([np.concatenate([topo.level1_index(s),
+                                      int_off[s] + np.arange((k - 1) * b)]) for s in subs])
+        groups.append((E, np.stack([rs.Gamma[s] for s in subs]), b, k))
+
+    def KK(x):
+        y = np.zeros_like(x)
+        for E, G, b, k in groups:
+            U = x[E].reshape(len(E), k, b)
+            Up = np.concatenate([U, np.zeros_like(U[:, :1])], axis=1)
+            D = Up[:, :-1] - Up[:, 1:]                    # (D U)_j = U_j - U_{j+1}
+            GD = np.einsum("sjab,sjb->sja", G, D)
+            out = GD.copy()
+            out[:, 1:] -= GD[:, :-1]                      # D^T
+            np.add.at(y, E.ravel(), out.reshape(-1))
+        return y
+
+    op = spla.LinearOperator((n, n), matvec=lambda v: C.T @ KK(C @ np.ravel(v)), dtype=np.float64)
+    return float(spla.eigsh(op, k=1, which="LA", tol=tol, return_eigenvectors=False)[0])
 
 
 # ----------------------------------------------------------------------------

@@ -36,14 +36,16 @@ class SubdomainROM:
         """Projected rows (k, b) of a nodal vector (Algorithm 1 step 1.4)."""
         return project.project(self._V, self._Qh, self.G, self.mass, vec)
 
-    def drop_basis(self):
-        self._V = self._Qh = None
 
 
 def build(problem, keep=False, subs=None):
     """Build the ROM set of ``problem``.  ``keep`` keeps every subdomain's
     ``SubdomainROM`` (with V) in ``.subroms``; ``subs`` restricts the build
-    to a list of subdomains (their coefficients only, for sampling)."""
+    to a list of subdomains (their coefficients only, for sampling).
+
+    Subdomains whose operator inputs are identical (same box shape, same
+    velocity block, same face mode counts, same k) have identical ROMs; the
+    build is done once for each distinct input and reused."""
     topo = faces.Topology(problem)
     gmass = fine.global_mass_ijk(problem)
     h = problem.h
@@ -55,32 +57,45 @@ def build(problem, keep=False, subs=None):
     src = [dict() for _ in src_w]
     rec = [dict() for _ in rec_w]
     kept = {}
+    built = {}
     for s in (range(problem.nsub) if subs is None else subs):
-        sr = SubdomainROM(problem, topo, s, keep_basis=keep)
+        box = problem.sub_box(s)
+        x0, x1, y0, y1, z0, z1 = box
+        key = (x1 - x0, y1 - y0, z1 - z0, tuple(int(v) for v in topo.mf[s]),
+               int(problem.k_sub[s]), problem.c[z0:z1, y0:y1, x0:x1].tobytes())
+        if key not in built:
+            built[key] = SubdomainROM(problem, topo, s, keep_basis=keep)
+        sr = built[key]
         Gam[s] = np.stack(sr.Gamma)
         Gh[s] = np.stack(sr.Gammahat)
+        vecs, where = [], []
         for q, (nodes, w) in enumerate(src_w):
-            v = project.local_share(sr.box, gmass, sr.mass, nodes, w)
+            v = project.local_share(box, gmass, sr.mass, nodes, w)
             if v is not None:
-                src[q][s] = sr.rows(v)
+                vecs.append(v)
+                where.append((src, q))
         for r, (nodes, w) in enumerate(rec_w):
-            v = project.local_share(sr.box, gmass, sr.mass, nodes, w)
+            v = project.local_share(box, gmass, sr.mass, nodes, w)
             if v is not None:
-                rec[r][s] = sr.rows(v)
+                vecs.append(v)
+                where.append((rec, r))
+        if vecs:
+            rows = sr.rows(np.stack(vecs, axis=1))
+            for (dst, i), row in zip(where, rows):
+                dst[i][s] = row
         if keep:
             kept[s] = sr
-        else:
-            sr.drop_basis()
     if subs is not None:
         return topo, Gam, Gh, kept
     rs = coupled.RomSet(topo, Gam, Gh, src, rec)
     rs.subroms = kept
+    rs.distinct = len(built)
     return rs
 
 
 def rom_dt(rs, safety=0.9):
     """``safety * dt_CFL`` of the coupled ROM system (0.9 by default)."""
-    return safety * coupled.Assembled(rs).cfl_dt()
+    return safety * 2.0 / np.sqrt(coupled.lambda_max(rs))
 
 
 # ----------------------------------------------------------------------------

@@ -45,8 +45,13 @@ def local_share(box, global_mass, sub_mass, nodes, weights):
 
 
 def project(V, Qh, G, sub_mass, vec):
-    """``p_j = G_j^{-T} Qh_j^T V^T M^{-1/2} vec`` for j = 1..k; returns (k, b)."""
-    y = Qh.T @ (V.T @ (vec / np.sqrt(sub_mass)))
+    """``p_j = G_j^{-T} Qh_j^T V^T M^{-1/2} vec`` for j = 1..k; returns (k, b).
+    ``vec`` may also be a matrix of column vectors (N, n): returns (n, k, b)."""
+    one = vec.ndim == 1
+    X = vec[:, None] if one else vec
+    Y = Qh.T @ (V.T @ (X / np.sqrt(sub_mass)[:, None]))
     b = G[0].shape[0]
     k = len(G)
-    return np.stack([np.linalg.solve(G[j].T, y[j * b:(j + 1) * b]) for j in range(k)])
+    out = np.stack([np.linalg.solve(G[j].T, Y[j * b:(j + 1) * b]) for j in range(k)])  # (k,b,n)
+    out = np.moveaxis(out, 2, 0)
+    return out[0] if one else out

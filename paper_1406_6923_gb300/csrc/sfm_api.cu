@@ -1,0 +1,640 @@
+// Host side of the libsfm C ABI: handle, topology, coefficient/source/
+// receiver upload, precision caches and the stepping driver.
+#include "sfm_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(sfm_handle* h, int code, const std::string& msg) {
+    if (h) h->err = msg; else g_err = msg;
+    return code;
+}
+
+int cuda_fail(sfm_handle* h, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return fail(h, SFM_ERR_NOMEM, m);
+    return fail(h, SFM_ERR_CUDA, m);
+}
+
+#define CK(h, call)                                              \
+    do {                                                         \
+        cudaError_t e__ = (call);                                \
+        if (e__ != cudaSuccess) return cuda_fail((h), e__, #call); \
+    } while (0)
+
+template <typename P>
+void dfree(P*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+template <typename P>
+cudaError_t dalloc(P*& p, size_t count) {
+    dfree(p);
+    if (count == 0) count = 1;
+    return cudaMalloc((void**)&p, count * sizeof(P));
+}
+
+template <typename P>
+cudaError_t upload(P*& d, const P* host, size_t count, cudaStream_t st) {
+    cudaError_t e = dalloc(d, count);
+    if (e != cudaSuccess) return e;
+    if (count) e = cudaMemcpyAsync(d, host, count * sizeof(P), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);
+}
+
+// Converted copies of the FP64 master data in one compute precision.
+template <typename T>
+struct Cache {
+    T *coef = nullptr, *H = nullptr, *src = nullptr, *rrows = nullptr;
+    bool valid = false;
+    void release() {
+        dfree(coef); dfree(H); dfree(src); dfree(rrows);
+        valid = false;
+    }
+};
+
+// Run buffers in one precision, grown on demand.
+template <typename T>
+struct RunBufs {
+    T *U[3] = {nullptr, nullptr, nullptr}, *dU = nullptr, *mail[2] = {nullptr, nullptr};
+    T *wavelet = nullptr, *partial = nullptr;
+    size_t n_state = 0, n_mail = 0, n_wav = 0, n_part = 0;
+    void release() {
+        for (auto& u : U) dfree(u);
+        dfree(dU); dfree(mail[0]); dfree(mail[1]); dfree(wavelet); dfree(partial);
+        n_state = n_mail = n_wav = n_part = 0;
+    }
+};
+
+}  // namespace
+
+struct sfm_ext {
+    Cache<float> c32;
+    Cache<double> c64;
+    Cache<float2> c2;
+    RunBufs<float> r32;
+    RunBufs<double> r64;
+    RunBufs<float2> r2;
+    double* d_traces = nullptr;
+    size_t n_traces = 0;
+    int* d_bad = nullptr;
+    unsigned long long timeout_ns = 2000000000ull;
+    int skip_arrive = -1;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+static sfm_ext* ext(sfm_handle* h) { return reinterpret_cast<sfm_ext*>(h->scratch); }
+
+static void invalidate(sfm_handle* h) {
+    ext(h)->c32.release();
+    ext(h)->c64.release();
+    ext(h)->c2.release();
+}
+
+extern "C" {
+
+int sfm_create(sfm_handle** out, int device) {
+    if (!out) return fail(nullptr, SFM_ERR_ARG, "sfm_create: NULL handle pointer");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(nullptr, SFM_ERR_ARG, "sfm_create: bad device");
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaSetDevice");
+    sfm_handle* h = new (std::nothrow) sfm_handle();
+    if (!h) return fail(nullptr, SFM_ERR_NOMEM, "sfm_create: host allocation");
+    h->device = device;
+    h->scratch = new (std::nothrow) sfm_ext();
+    if (!h->scratch) { delete h; return fail(nullptr, SFM_ERR_NOMEM, "sfm_create: host allocation"); }
+    sfm_ext* x = ext(h);
+    if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreate(&x->ev0)) != cudaSuccess ||
+        (e = cudaEventCreate(&x->ev1)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&h->d_bar, sizeof(unsigned int))) != cudaSuccess ||
+        (e = cudaMalloc((void**)&h->d_err, sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc((void**)&x->d_bad, sizeof(int))) != cudaSuccess) {
+        int rc = cuda_fail(nullptr, e, "sfm_create");
+        sfm_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return SFM_OK;
+}
+
+int sfm_destroy(sfm_handle* h) {
+    if (!h) return SFM_OK;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    sfm_ext* x = ext(h);
+    if (x) {
+        x->c32.release(); x->c64.release(); x->c2.release();
+        x->r32.release(); x->r64.release(); x->r2.release();
+        dfree(x->d_traces); dfree(x->d_bad);
+        if (x->ev0) cudaEventDestroy(x->ev0);
+        if (x->ev1) cudaEventDestroy(x->ev1);
+        delete x;
+    }
+    sfm::free_build(h);
+    dfree(h->d_b); dfree(h->d_k); dfree(h->d_face_off); dfree(h->d_nbr);
+    dfree(h->d_coef_off); dfree(h->d_H_off); dfree(h->d_state_off); dfree(h->d_mail_off);
+    dfree(h->d_coef64); dfree(h->d_H64); dfree(h->d_src64); dfree(h->d_src_off);
+    dfree(h->d_rrows64); dfree(h->d_rp_sub); dfree(h->d_rec_ptr); dfree(h->d_rec_pairs);
+    dfree(h->d_rp_off); dfree(h->d_bar); dfree(h->d_err);
+    if (h->stream && h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return SFM_OK;
+}
+
+const char* sfm_last_error(const sfm_handle* h) {
+    return h ? h->err.c_str() : g_err.c_str();
+}
+
+int sfm_set_stream(sfm_handle* h, void* stream) {
+    if (!h) return fail(nullptr, SFM_ERR_ARG, "sfm_set_stream: NULL handle");
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    h->stream = nullptr;
+    h->own_stream = false;
+    if (stream) {
+        h->stream = (cudaStream_t)stream;      // the caller's: never destroyed here
+    } else {
+        CK(h, cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+        h->own_stream = true;
+    }
+    return SFM_OK;
+}
+
+int sfm_set_topology(sfm_handle* h, int nsub, const int* k_sub, const int* m_face,
+                     const int* nbr) {
+    if (!h) return fail(nullptr, SFM_ERR_ARG, "NULL handle");
+    if (nsub <= 0 || !k_sub || !m_face || !nbr)
+        return fail(h, SFM_ERR_ARG, "sfm_set_topology: bad arguments");
+    CK(h, cudaSetDevice(h->device));
+    for (int s = 0; s < nsub; ++s) {
+        if (k_sub[s] < 1) return fail(h, SFM_ERR_ARG, "sfm_set_topology: k < 1");
+        int b = 0;
+        for (int f = 0; f < 6; ++f) {
+            const int m = m_face[s * 6 + f], t = nbr[s * 6 + f];
+            if (m < 0 || m > SFM_MAX_FACE_M)
+                return fail(h, SFM_ERR_ARG, "sfm_set_topology: face mode count out of range");
+            if (t >= nsub || t < -1 || t == s)
+                return fail(h, SFM_ERR_ARG, "sfm_set_topology: bad neighbour index");
+            if (t >= 0 && (nbr[t * 6 + (f ^ 1)] != s || m_face[t * 6 + (f ^ 1)] != m))
+                return fail(h, SFM_ERR_ARG, "sfm_set_topology: neighbours not symmetric");
+            b += m;
+        }
+        if (b == 0) return fail(h, SFM_ERR_ARG, "sfm_set_topology: subdomain with b = 0");
+        if ((long long)b * k_sub[s] > 256 * 64)
+            return fail(h, SFM_ERR_ARG, "sfm_set_topology: k*b too large");
+    }
+    h->nsub = nsub;
+    h->k.assign(k_sub, k_sub + nsub);
+    h->mface.assign(m_face, m_face + 6 * nsub);
+    h->nbr.assign(nbr, nbr + 6 * nsub);
+    h->b.assign(nsub, 0);
+    h->face_off.assign(7 * nsub, 0);
+    h->coef_off.assign(nsub, 0);
+    h->H_off.assign(6 * nsub, -1);
+    h->state_off.assign(nsub, 0);
+    h->mail_off.assign(nsub, 0);
+    long long co = 0, ho = 0, so = 0, mo = 0;
+    h->kmax = h->bmax = 0;
+    for (int s = 0; s < nsub; ++s) {
+        int b = 0;
+        for (int f = 0; f < 6; ++f) {
+            h->face_off[s * 7 + f] = b;
+            const int m = m_face[s * 6 + f];
+            if (m > 0) { h->H_off[s * 6 + f] = ho; ho += (long long)m * m; }
+            b += m;
+        }
+        h->face_off[s * 7 + 6] = b;
+        h->b[s] = b;
+        h->coef_off[s] = co;
+        co += 2LL * h->k[s] * b * b;
+        h->state_off[s] = so;
+        so += (long long)h->k[s] * b;
+        h->mail_off[s] = mo;
+        mo += b;
+        h->kmax = std::max(h->kmax, h->k[s]);
+        h->bmax = std::max(h->bmax, b);
+    }
+    h->ncoef = co; h->nH = ho; h->nstate = so; h->nmail = mo;
+    cudaStream_t st = h->stream;
+    CK(h, upload(h->d_b, h->b.data(), nsub, st));
+    CK(h, upload(h->d_k, h->k.data(), nsub, st));
+    CK(h, upload(h->d_face_off, h->face_off.data(), 7 * (size_t)nsub, st));
+    CK(h, upload(h->d_nbr, h->nbr.data(), 6 * (size_t)nsub, st));
+    CK(h, upload(h->d_coef_off, h->coef_off.data(), nsub, st));
+    CK(h, upload(h->d_H_off, h->H_off.data(), 6 * (size_t)nsub, st));
+    CK(h, upload(h->d_state_off, h->state_off.data(), nsub, st));
+    CK(h, upload(h->d_mail_off, h->mail_off.data(), nsub, st));
+    h->have_coef = h->have_src = h->have_rec = false;
+    invalidate(h);
+    return SFM_OK;
+}
+
+}  // extern "C"
+
+static int set_coeffs_common(sfm_handle* h, const double* coeffs, bool on_device) {
+    CK(h, cudaSetDevice(h->device));
+    cudaStream_t st = h->stream;
+    if (on_device) {
+        CK(h, dalloc(h->d_coef64, (size_t)h->ncoef));
+        CK(h, cudaMemcpyAsync(h->d_coef64, coeffs, (size_t)h->ncoef * sizeof(double),
+                              cudaMemcpyDeviceToDevice, st));
+    } else {
+        CK(h, upload(h->d_coef64, coeffs, (size_t)h->ncoef, st));
+    }
+    CK(h, dalloc(h->d_H64, (size_t)h->nH));
+    std::vector<long long> gh1(h->nsub);
+    for (int s = 0; s < h->nsub; ++s)
+        gh1[s] = h->coef_off[s] + (long long)h->k[s] * h->b[s] * h->b[s];
+    long long* d_gh1 = nullptr;
+    CK(h, upload(d_gh1, gh1.data(), gh1.size(), st));
+    CK(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+    cudaError_t e = sfm::launch_face_H(h->d_coef64, d_gh1, h->d_b, h->d_face_off, h->d_nbr,
+                                       h->d_H_off, h->d_H64, h->nsub, h->d_err, st);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dfree(d_gh1);
+    if (e != cudaSuccess) return cuda_fail(h, e, "face coupling H_f");
+    invalidate(h);
+    if (herr != 0) {
+        h->have_coef = false;
+        return fail(h, herr, "sfm_set_coeffs: a face block of Gammahat_1 is not SPD");
+    }
+    h->have_coef = true;
+    return SFM_OK;
+}
+
+namespace sfm {
+int set_topology_internal(sfm_handle* h, int nsub, const int* k_sub, const int* m_face,
+                          const int* nbr) {
+    return sfm_set_topology(h, nsub, k_sub, m_face, nbr);
+}
+int set_coeffs_device(sfm_handle* h, const double* d_coeffs) {
+    return set_coeffs_common(h, d_coeffs, true);
+}
+}  // namespace sfm
+
+extern "C" {
+
+int sfm_set_coeffs(sfm_handle* h, const double* coeffs, size_t count) {
+    if (!h) return fail(nullptr, SFM_ERR_ARG, "NULL handle");
+    if (h->nsub == 0) return fail(h, SFM_ERR_STATE, "sfm_set_coeffs: no topology");
+    if (!coeffs || count != (size_t)h->ncoef)
+        return fail(h, SFM_ERR_ARG, "sfm_set_coeffs: count does not match the topology");
+    return set_coeffs_common(h, coeffs, false);
+}
+
+int sfm_get_coeffs(sfm_handle* h, double* coeffs, size_t count, size_t* needed) {
+    if (!h) return fail(nullptr, SFM_ERR_ARG, "NULL handle");
+    if (needed) *needed = (size_t)h->ncoef;
+    if (!coeffs) return SFM_OK;
+    if (!h->have_coef) return fail(h, SFM_ERR_STATE, "sfm_get_coeffs: no coefficients");
+    if (count < (size_t)h->ncoef) return fail(h, SFM_ERR_ARG, "sfm_get_coeffs: buffer too small");
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaMemcpyAsync(coeffs, h->d_coef64, h->ncoef * sizeof(double), cudaMemcpyDeviceToHost,
+                          h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return SFM_OK;
+}
+
+int sfm_set_sources(sfm_handle* h, int nshots, int npairs, const int* pair_shot,
+                    const int* pair_sub, const double* rows) {
+    if (!h) return fail(nullptr, SFM_ERR_ARG, "NULL handle");
+    if (h->nsub == 0) return fail(h, SFM_ERR_STATE, "sfm_set_sources: no topology");
+    if (nshots < 1 || npairs < 0 || (npairs > 0 && (!pair_shot || !pair_sub || !rows)))
+        return fail(h, SFM_ERR_ARG, "sfm_set_sources: bad arguments");
+    CK(h, cudaSetDevice(h->device));
+    std::vector<long long> off((size_t)nshots * h->nsub, -1);
+    long long o = 0;
+    for (int i = 0; i < npairs; ++i) {
+        const int q = pair_shot[i], s = pair_sub[i];
+        if (q < 0 || q >= nshots || s < 0 || s >= h->nsub)
+            return fail(h, SFM_ERR_ARG, "sfm_set_sources: pair index out of range");
+        if (off[(size_t)q * h->nsub + s] >= 0)
+            return fail(h, SFM_ERR_ARG, "sfm_set_sources: duplicate (shot, subdomain) pair");
+        off[(size_t)q * h->nsub + s] = o;
+        o += (long long)h->k[s] * h->b[s];
+    }
+    h->nshots = nshots;
+    h->src_off = off;
+    h->nsrc = o;
+    CK(h, upload(h->d_src64, rows, (size_t)o, h->stream));
+    CK(h, upload(h->d_src_off, off.data(), off.size(), h->stream));
+    h->have_src = true;
+    invalidate(h);
+    return SFM_OK;
+}
+
+int sfm_set_receivers(sfm_handle* h, int nrec, int npairs, const int* pair_rec,
+                      const int* pair_sub, const double* rows) {
+    if (!h) return fail(nullptr, SFM_ERR_ARG, "NULL handle");
+    if (h->nsub == 0) return fail(h, SFM_ERR_STATE, "sfm_set_receivers: no topology");
+    if (nrec < 1 || npairs < 0 || (npairs > 0 && (!pair_rec || !pair_sub || !rows)))
+        return fail(h, SFM_ERR_ARG, "sfm_set_receivers: bad arguments");
+    CK(h, cudaSetDevice(h->device));
+    std::vector<int> rsub(npairs), rrec(npairs);
+    std::vector<long long> roff(npairs);
+    std::vector<int> cnt(nrec + 1, 0);
+    long long o = 0;
+    for (int i = 0; i < npairs; ++i) {
+        const int r = pair_rec[i], s = pair_sub[i];
+        if (r < 0 || r >= nrec || s < 0 || s >= h->nsub)
+            return fail(h, SFM_ERR_ARG, "sfm_set_receivers: pair index out of range");
+        rsub[i] = s; rrec[i] = r; roff[i] = o;
+        o += (long long)h->k[s] * h->b[s];
+        cnt[r + 1]++;
+    }
+    for (int r = 0; r < nrec; ++r) cnt[r + 1] += cnt[r];
+    std::vector<int> pairs(npairs), fill(cnt.begin(), cnt.end() - 1);
+    for (int i = 0; i < npairs; ++i) pairs[fill[rrec[i]]++] = i;
+    h->nrec = nrec; h->nrpairs = npairs;
+    h->rp_sub = rsub; h->rp_rec = rrec; h->rp_off = roff; h->nrrow = o;
+    cudaStream_t st = h->stream;
+    CK(h, upload(h->d_rrows64, rows, (size_t)o, st));
+    CK(h, upload(h->d_rp_sub, rsub.data(), rsub.size(), st));
+    CK(h, upload(h->d_rp_off, roff.data(), roff.size(), st));
+    CK(h, upload(h->d_rec_ptr, cnt.data(), cnt.size(), st));
+    CK(h, upload(h->d_rec_pairs, pairs.data(), pairs.size(), st));
+    h->have_rec = true;
+    invalidate(h);
+    return SFM_OK;
+}
+
+int sfm_debug_set(sfm_handle* h, int key, long long value) {
+    if (!h) return fail(nullptr, SFM_ERR_ARG, "NULL handle");
+    if (key == 1) { ext(h)->timeout_ns = (unsigned long long)value; return SFM_OK; }
+    if (key == 2) { ext(h)->skip_arrive = (int)value; return SFM_OK; }
+    return fail(h, SFM_ERR_ARG, "sfm_debug_set: unknown key");
+}
+
+int sfm_last_launches(const sfm_handle* h, int* launches) {
+    if (!h || !launches) return SFM_ERR_ARG;
+    *launches = h->last_launches;
+    return SFM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+
+template <typename T>
+static Cache<T>& cache_of(sfm_handle* h);
+template <>
+Cache<float>& cache_of<float>(sfm_handle* h) { return ext(h)->c32; }
+template <>
+Cache<double>& cache_of<double>(sfm_handle* h) { return ext(h)->c64; }
+template <>
+Cache<float2>& cache_of<float2>(sfm_handle* h) { return ext(h)->c2; }
+template <typename T>
+static RunBufs<T>& bufs_of(sfm_handle* h);
+template <>
+RunBufs<float>& bufs_of<float>(sfm_handle* h) { return ext(h)->r32; }
+template <>
+RunBufs<double>& bufs_of<double>(sfm_handle* h) { return ext(h)->r64; }
+template <>
+RunBufs<float2>& bufs_of<float2>(sfm_handle* h) { return ext(h)->r2; }
+
+template <class P>
+static int prepare(sfm_handle* h) {
+    using T = typename P::S;
+    Cache<T>& c = cache_of<T>(h);
+    if (c.valid) return SFM_OK;
+    c.release();
+    cudaStream_t st = h->stream;
+    CK(h, dalloc(c.coef, (size_t)h->ncoef));
+    CK(h, dalloc(c.H, (size_t)h->nH));
+    CK(h, dalloc(c.src, (size_t)h->nsrc));
+    CK(h, dalloc(c.rrows, (size_t)h->nrrow));
+    CK(h, sfm::launch_convert<P>(h->d_coef64, c.coef, (size_t)h->ncoef, st));
+    CK(h, sfm::launch_convert<P>(h->d_H64, c.H, (size_t)h->nH, st));
+    CK(h, sfm::launch_convert<P>(h->d_src64, c.src, (size_t)h->nsrc, st));
+    CK(h, sfm::launch_convert<P>(h->d_rrows64, c.rrows, (size_t)h->nrrow, st));
+    CK(h, cudaStreamSynchronize(st));
+    c.valid = true;
+    return SFM_OK;
+}
+
+template <typename P>
+static cudaError_t grow(P*& p, size_t& have, size_t need) {
+    if (need <= have && p) return cudaSuccess;
+    cudaError_t e = dalloc(p, need);
+    have = (e == cudaSuccess) ? need : 0;
+    return e;
+}
+
+template <class P>
+static int run_impl(sfm_handle* h, double dt, int nsteps, const double* wavelet, double* traces,
+                    int flags, double* kernel_ms) {
+    using T = typename P::S;
+    sfm_ext* x = ext(h);
+    int rc = prepare<P>(h);
+    if (rc != SFM_OK) return rc;
+    Cache<T>& c = cache_of<T>(h);
+    RunBufs<T>& r = bufs_of<T>(h);
+    cudaStream_t st = h->stream;
+    const size_t nst = (size_t)h->nshots * h->nstate;
+    const size_t nml = (size_t)h->nshots * h->nmail;
+    const size_t nwav = (size_t)h->nshots * nsteps;
+    const size_t npart = (size_t)h->nshots * (nsteps + 1) * h->nrpairs;
+    const size_t ntr = (size_t)h->nshots * h->nrec * (nsteps + 1);
+    size_t have_state = r.n_state;
+    for (int i = 0; i < 3; ++i) { size_t hs = have_state; CK(h, grow(r.U[i], hs, nst)); }
+    { size_t hs = have_state; CK(h, grow(r.dU, hs, nst)); r.n_state = hs; }
+    size_t have_mail = r.n_mail;
+    { size_t hm = have_mail; CK(h, grow(r.mail[0], hm, nml)); }
+    { size_t hm = have_mail; CK(h, grow(r.mail[1], hm, nml)); r.n_mail = hm; }
+    CK(h, grow(r.wavelet, r.n_wav, nwav));
+    CK(h, grow(r.partial, r.n_part, npart));
+    double* d_traces = traces;
+    if (!(flags & SFM_DEVICE_PTR)) {
+        CK(h, grow(x->d_traces, x->n_traces, ntr));
+        d_traces = x->d_traces;
+    }
+    // wavelet to the compute precision
+    const double* d_wav64 = wavelet;
+    double* tmp64 = nullptr;
+    if (!(flags & SFM_DEVICE_PTR)) {
+        CK(h, dalloc(tmp64, nwav));
+        CK(h, cudaMemcpyAsync(tmp64, wavelet, nwav * sizeof(double), cudaMemcpyHostToDevice, st));
+        d_wav64 = tmp64;
+    }
+    int launches = 0;
+    CK(h, sfm::launch_convert<P>(d_wav64, r.wavelet, nwav, st));
+    ++launches;
+    for (int i = 0; i < 3; ++i) CK(h, cudaMemsetAsync(r.U[i], 0, nst * sizeof(T), st));
+    CK(h, cudaMemsetAsync(r.dU, 0, nst * sizeof(T), st));
+    CK(h, cudaMemsetAsync(h->d_bar, 0, sizeof(unsigned int), st));
+    CK(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+    CK(h, cudaMemsetAsync(x->d_bad, 0, sizeof(int), st));
+
+    sfm::StepParams<T> p{};
+    p.nsub = h->nsub; p.nshots = h->nshots; p.nunits = h->nshots * h->nsub; p.nsteps = nsteps;
+    p.kmax = h->kmax; p.bmax = h->bmax;
+    p.sub_b = h->d_b; p.sub_k = h->d_k; p.coef_off = h->d_coef_off; p.coef = c.coef;
+    p.face_off = h->d_face_off; p.nbr = h->d_nbr; p.H_off = h->d_H_off; p.H = c.H;
+    p.state_off = h->d_state_off; p.state_stride = h->nstate;
+    for (int i = 0; i < 3; ++i) p.U[i] = r.U[i];
+    p.dU = r.dU;
+    p.mail_off = h->d_mail_off; p.mail_stride = h->nmail; p.mail0 = r.mail[0]; p.mail1 = r.mail[1];
+    p.src_off = h->d_src_off; p.src = c.src; p.wavelet = r.wavelet;
+    p.nrec = h->nrec; p.nrpairs = h->nrpairs; p.rp_sub = h->d_rp_sub; p.rp_off = h->d_rp_off;
+    p.rrows = c.rrows; p.partial = r.partial;
+    p.dt2 = dt * dt;
+    p.bar = h->d_bar; p.err = h->d_err; p.timeout_ns = x->timeout_ns;
+    p.skip_arrive = x->skip_arrive;
+
+    const int block = 256;
+    int gmax = 0;
+    if (sfm::step_max_grid<P>(block, sfm::step_smem_bytes<P>(h->kmax, h->bmax, block), &gmax) != 0) {
+        dfree(tmp64);
+        return fail(h, SFM_ERR_ARG, "sfm_run: subdomain blocks too large for shared memory");
+    }
+    const int grid = std::min(gmax, std::max(p.nunits, 1));
+    CK(h, cudaEventRecord(x->ev0, st));
+    cudaError_t e = sfm::launch_step<P>(p, block, grid, st);
+    if (e != cudaSuccess) { dfree(tmp64); return cuda_fail(h, e, "step kernel launch"); }
+    ++launches;
+    CK(h, cudaEventRecord(x->ev1, st));
+    e = sfm::launch_reduce_traces<P>(r.partial, h->d_rec_ptr, h->d_rec_pairs, h->nshots, nsteps,
+                                     h->nrec, h->nrpairs, d_traces, x->d_bad, st);
+    if (e != cudaSuccess) { dfree(tmp64); return cuda_fail(h, e, "trace reduction launch"); }
+    ++launches;
+    int herr = 0, bad = 0;
+    CK(h, cudaMemcpyAsync(&herr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(h, cudaMemcpyAsync(&bad, x->d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (!(flags & SFM_DEVICE_PTR))
+        CK(h, cudaMemcpyAsync(traces, d_traces, ntr * sizeof(double), cudaMemcpyDeviceToHost, st));
+    e = cudaStreamSynchronize(st);
+    dfree(tmp64);
+    if (e != cudaSuccess) return cuda_fail(h, e, "stepping");
+    h->last_launches = launches;
+    if (kernel_ms) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, x->ev0, x->ev1);
+        *kernel_ms = ms;
+    }
+    if (herr == SFM_ERR_TIMEOUT) return fail(h, SFM_ERR_TIMEOUT, "device-wide barrier timed out");
+    if (herr != 0) return fail(h, herr, "device error during stepping");
+    if (bad) return fail(h, SFM_ERR_UNSTABLE, "non-finite traces (time step above the CFL limit?)");
+    return SFM_OK;
+}
+
+extern "C" int sfm_run(sfm_handle* h, int precision, double dt, int nsteps, const double* wavelet,
+                       double* traces, int flags, double* kernel_ms) {
+    if (!h) return fail(nullptr, SFM_ERR_ARG, "NULL handle");
+    if (!h->have_coef || !h->have_src || !h->have_rec)
+        return fail(h, SFM_ERR_STATE, "sfm_run: coefficients, sources and receivers must be set");
+    if (nsteps < 1 || !(dt > 0.0) || !wavelet || !traces)
+        return fail(h, SFM_ERR_ARG, "sfm_run: bad arguments");
+    CK(h, cudaSetDevice(h->device));
+    if (precision == SFM_FP64)
+        return run_impl<sfm::PolF64>(h, dt, nsteps, wavelet, traces, flags, kernel_ms);
+    if (precision == SFM_FP32)
+        return run_impl<sfm::PolF32>(h, dt, nsteps, wavelet, traces, flags, kernel_ms);
+    if (precision == SFM_FP32X2)
+        return run_impl<sfm::PolF32x2>(h, dt, nsteps, wavelet, traces, flags, kernel_ms);
+    return fail(h, SFM_ERR_ARG, "sfm_run: unknown precision");
+}
+
+// Largest eigenvalue of MM^{-1} KK by power iteration.  One FP64 step of the
+// stepping kernel from state X with zero increment, zero source and dt = 1
+// leaves the increment equal to the acceleration a(X) = -MM^{-1} KK X, so the
+// kernel that steps the system is also the operator of this iteration.
+extern "C" int sfm_cfl_dt(sfm_handle* h, int iters, double* lambda_max, double* dt_cfl) {
+    if (!h) return fail(nullptr, SFM_ERR_ARG, "NULL handle");
+    if (!h->have_coef) return fail(h, SFM_ERR_STATE, "sfm_cfl_dt: no coefficients");
+    if (iters < 1) return fail(h, SFM_ERR_ARG, "sfm_cfl_dt: iters < 1");
+    CK(h, cudaSetDevice(h->device));
+    sfm_ext* x = ext(h);
+    // sources/receivers are not needed: convert what exists (possibly empty)
+    int rc = prepare<sfm::PolF64>(h);
+    if (rc != SFM_OK) return rc;
+    Cache<double>& c = x->c64;
+    cudaStream_t st = h->stream;
+    const size_t n = (size_t)h->nstate;
+    double *U[3] = {nullptr, nullptr, nullptr}, *dU = nullptr, *mail0 = nullptr, *mail1 = nullptr,
+           *wav = nullptr, *X = nullptr, *ss = nullptr;
+    long long* soff = nullptr;
+    auto cleanup = [&]() {
+        for (auto& u : U) dfree(u);
+        dfree(dU); dfree(mail0); dfree(mail1); dfree(wav); dfree(X); dfree(ss); dfree(soff);
+    };
+#define CKC(call)                                                              \
+    do {                                                                       \
+        cudaError_t e__ = (call);                                              \
+        if (e__ != cudaSuccess) { cleanup(); return cuda_fail(h, e__, #call); } \
+    } while (0)
+    for (auto& u : U) CKC(dalloc(u, n));
+    CKC(dalloc(dU, n));
+    CKC(dalloc(mail0, (size_t)h->nmail));
+    CKC(dalloc(mail1, (size_t)h->nmail));
+    CKC(dalloc(wav, 1));
+    CKC(dalloc(X, n));
+    CKC(dalloc(ss, 1));
+    std::vector<long long> none(h->nsub, -1);
+    CKC(upload(soff, none.data(), none.size(), st));
+    std::vector<double> ones(n, 1.0);
+    CKC(cudaMemcpyAsync(X, ones.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+    CKC(cudaMemsetAsync(wav, 0, sizeof(double), st));
+
+    sfm::StepParams<double> p{};
+    p.nsub = h->nsub; p.nshots = 1; p.nunits = h->nsub; p.nsteps = 1;
+    p.kmax = h->kmax; p.bmax = h->bmax;
+    p.sub_b = h->d_b; p.sub_k = h->d_k; p.coef_off = h->d_coef_off; p.coef = c.coef;
+    p.face_off = h->d_face_off; p.nbr = h->d_nbr; p.H_off = h->d_H_off; p.H = c.H;
+    p.state_off = h->d_state_off; p.state_stride = h->nstate;
+    for (int i = 0; i < 3; ++i) p.U[i] = U[i];
+    p.dU = dU;
+    p.mail_off = h->d_mail_off; p.mail_stride = h->nmail; p.mail0 = mail0; p.mail1 = mail1;
+    p.src_off = soff; p.src = c.src; p.wavelet = wav;
+    p.nrec = 0; p.nrpairs = 0; p.rp_sub = nullptr; p.rp_off = nullptr; p.rrows = nullptr;
+    p.partial = nullptr;
+    p.dt2 = 1.0;
+    p.bar = h->d_bar; p.err = h->d_err; p.timeout_ns = x->timeout_ns; p.skip_arrive = -1;
+    const int block = 256;
+    int gmax = 0;
+    if (sfm::step_max_grid<sfm::PolF64>(block,
+                                        sfm::step_smem_bytes<sfm::PolF64>(h->kmax, h->bmax, block),
+                                        &gmax) != 0) {
+        cleanup();
+        return fail(h, SFM_ERR_ARG, "sfm_cfl_dt: subdomain blocks too large for shared memory");
+    }
+    const int grid = std::min(gmax, h->nsub);
+    for (int it = 0; it < iters; ++it) {
+        CKC(cudaMemcpyAsync(U[0], X, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CKC(cudaMemsetAsync(dU, 0, n * sizeof(double), st));
+        CKC(cudaMemsetAsync(h->d_bar, 0, sizeof(unsigned int), st));
+        CKC(cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+        CKC(sfm::launch_step<sfm::PolF64>(p, block, grid, st));
+        CKC(sfm::launch_sumsq(dU, n, ss, st));
+        CKC(sfm::launch_scale(dU, X, n, ss, st));
+    }
+    double sumsq = 0.0;
+    int herr = 0;
+    CKC(cudaMemcpyAsync(&sumsq, ss, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CKC(cudaMemcpyAsync(&herr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CKC(cudaStreamSynchronize(st));
+#undef CKC
+    cleanup();
+    if (herr != 0) return fail(h, herr, "sfm_cfl_dt: device error");
+    // after the first iteration X has unit norm, so |a(X)| is the estimate
+    const double lam = (iters > 1) ? std::sqrt(sumsq) : std::sqrt(sumsq / (double)n);
+    if (lambda_max) *lambda_max = lam;
+    if (dt_cfl) *dt_cfl = 2.0 / std::sqrt(lam);
+    return SFM_OK;
+}

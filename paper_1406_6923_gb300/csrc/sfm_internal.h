@@ -1,0 +1,135 @@
+// Internal declarations shared by the translation units of libsfm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/sfm.h"
+#include "numeric.cuh"
+
+#define SFM_MAX_FACE_M 32      // largest m on one face (H_f kernel smem)
+
+namespace sfm {
+
+// Device-side description of the coupled ROM set in one compute precision
+// (T = the policy's storage type).  All offsets are element offsets into
+// the arrays they index.
+template <typename T>
+struct StepParams {
+    int nsub, nshots, nunits, nsteps;
+    int kmax, bmax;
+    const int* sub_b;            // [nsub]
+    const int* sub_k;            // [nsub]
+    const long long* coef_off;   // [nsub] -> Gamma_1..k, Gammahat_1..k (b*b each)
+    const T* coef;
+    const int* face_off;         // [nsub*7] start of face f inside the b-vector
+    const int* nbr;              // [nsub*6]
+    const long long* H_off;      // [nsub*6] -> m_f*m_f block, or -1
+    const T* H;
+    const long long* state_off;  // [nsub] offset of the k*b state of shot 0
+    long long state_stride;      // per shot
+    T* U[3];                     // state buffers, U^n lives in U[n % 3]
+    T* dU;                       // increments (one buffer, updated in place)
+    const long long* mail_off;   // [nsub] offset of the b-vector of shot 0
+    long long mail_stride;       // per shot
+    T* mail0;
+    T* mail1;
+    const long long* src_off;    // [nshots*nsub] offset of (k*b) source rows, -1 if none
+    const T* src;
+    const T* wavelet;            // [nshots][nsteps]
+    int nrec, nrpairs;
+    const int* rp_sub;           // [nrpairs] subdomain of each receiver pair
+    const long long* rp_off;     // [nrpairs] offset of its (k*b) row
+    const T* rrows;
+    T* partial;                  // [nshots][nsteps+1][nrpairs]
+    double dt2;
+    unsigned int* bar;           // grid barrier counter (zeroed before launch)
+    int* err;                    // device error word (0 = ok)
+    unsigned long long timeout_ns;
+    int skip_arrive;             // test hook: this block skips its barrier arrival (-1: none)
+};
+
+// launchers (step.cu); P is a number policy of numeric.cuh
+template <class P>
+cudaError_t launch_step(const StepParams<typename P::S>& p, int block, int grid, cudaStream_t st);
+template <class P>
+int step_max_grid(int block, size_t smem, int* grid_out);
+template <class P>
+size_t step_smem_bytes(int kmax, int bmax, int block);
+
+cudaError_t launch_face_H(const double* coef, const long long* gh1_off, const int* sub_b,
+                          const int* face_off, const int* nbr, const long long* H_off,
+                          double* H, int nsub, int* err, cudaStream_t st);
+
+template <class P>
+cudaError_t launch_convert(const double* in, typename P::S* out, size_t n, cudaStream_t st);
+
+// power-iteration helpers (FP64)
+cudaError_t launch_sumsq(const double* x, size_t n, double* out, cudaStream_t st);
+cudaError_t launch_scale(const double* x, double* y, size_t n, const double* sumsq,
+                         cudaStream_t st);
+
+template <class P>
+cudaError_t launch_reduce_traces(const typename P::S* partial, const int* rec_ptr,
+                                 const int* rec_pairs, int nshots, int nsteps, int nrec,
+                                 int nrpairs, double* traces, int* bad, cudaStream_t st);
+
+void free_build(sfm_handle* h);
+int set_topology_internal(sfm_handle* h, int nsub, const int* k_sub, const int* m_face,
+                          const int* nbr);
+int set_coeffs_device(sfm_handle* h, const double* d_coeffs);
+
+}  // namespace sfm
+
+// The opaque handle.
+struct sfm_handle {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = true;
+    std::string err;
+    int last_launches = 0;
+
+    // topology (host copies)
+    int nsub = 0;
+    std::vector<int> k, b, mface, nbr, face_off;     // face_off: nsub*7
+    std::vector<long long> coef_off, H_off, state_off, mail_off;
+    long long ncoef = 0, nH = 0, nstate = 0, nmail = 0;
+    int kmax = 0, bmax = 0;
+
+    // device copies of the topology
+    int *d_b = nullptr, *d_k = nullptr, *d_face_off = nullptr, *d_nbr = nullptr;
+    long long *d_coef_off = nullptr, *d_H_off = nullptr, *d_state_off = nullptr,
+              *d_mail_off = nullptr;
+
+    // FP64 master data
+    double* d_coef64 = nullptr;
+    double* d_H64 = nullptr;
+    bool have_coef = false;
+
+    int nshots = 0;
+    std::vector<long long> src_off;                  // nshots*nsub
+    long long nsrc = 0;
+    double* d_src64 = nullptr;
+    long long* d_src_off = nullptr;
+
+    int nrec = 0, nrpairs = 0;
+    std::vector<int> rp_sub, rp_rec;
+    std::vector<long long> rp_off;
+    long long nrrow = 0;
+    double* d_rrows64 = nullptr;
+    int *d_rp_sub = nullptr, *d_rec_ptr = nullptr, *d_rec_pairs = nullptr;
+    long long* d_rp_off = nullptr;
+    bool have_src = false, have_rec = false;
+
+    // offline builder state (builder.cu), NULL until sfm_set_model
+    void* build = nullptr;
+
+    // scratch owned by the handle, grown on demand
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    unsigned int* d_bar = nullptr;
+    int* d_err = nullptr;
+};

@@ -1,0 +1,227 @@
+"""Thin ctypes binding of ``libsfm`` (``include/sfm.h``).
+
+The functions carry the C names and only marshal arguments: every step of
+the method runs in the library's CUDA kernels.  A failing call raises
+:class:`SfmError` with the library's status code and message.  Loading fails
+loudly when ``libsfm.so`` has not been built: there is no fallback."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsfm.so")
+
+SFM_OK = 0
+SFM_ERR_ARG = -1
+SFM_ERR_CUDA = -2
+SFM_ERR_NOT_SPD = -3
+SFM_ERR_BREAKDOWN = -4
+SFM_ERR_UNSTABLE = -5
+SFM_ERR_TIMEOUT = -6
+SFM_ERR_NOMEM = -7
+SFM_ERR_STATE = -8
+
+SFM_FP64 = 0
+SFM_FP32 = 1
+SFM_FP32X2 = 2
+
+SFM_DEVICE_PTR = 1
+
+# every symbol include/sfm.h declares
+EXPORTS = ["sfm_create", "sfm_destroy", "sfm_last_error", "sfm_set_stream", "sfm_set_topology",
+           "sfm_set_coeffs", "sfm_get_coeffs", "sfm_set_sources", "sfm_set_receivers",
+           "sfm_run", "sfm_cfl_dt", "sfm_last_launches", "sfm_debug_set", "sfm_set_model",
+           "sfm_build_roms", "sfm_project_sources", "sfm_project_receivers"]
+
+
+class sfm_build_report(C.Structure):
+    _fields_ = [("seconds", C.c_double), ("cg_iterations_max", C.c_int),
+                ("cg_residual_max", C.c_double), ("krylov_min_ratio", C.c_double),
+                ("nclasses", C.c_int)]
+
+
+class SfmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libsfm error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+_i = C.c_int
+_p = C.c_void_p
+_ip = C.POINTER(C.c_int)
+_dp = C.POINTER(C.c_double)
+
+
+def load(path=LIB_PATH):
+    """Load ``libsfm.so`` (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libsfm.so not built at {path}; run paper_1406_6923_gb300._build")
+    lib = C.CDLL(path)
+    sig = {
+        "sfm_create": (_i, [C.POINTER(_p), _i]),
+        "sfm_destroy": (_i, [_p]),
+        "sfm_last_error": (C.c_char_p, [_p]),
+        "sfm_set_stream": (_i, [_p, _p]),
+        "sfm_set_topology": (_i, [_p, _i, _ip, _ip, _ip]),
+        "sfm_set_coeffs": (_i, [_p, _dp, C.c_size_t]),
+        "sfm_get_coeffs": (_i, [_p, _dp, C.c_size_t, C.POINTER(C.c_size_t)]),
+        "sfm_set_sources": (_i, [_p, _i, _i, _ip, _ip, _dp]),
+        "sfm_set_receivers": (_i, [_p, _i, _i, _ip, _ip, _dp]),
+        "sfm_run": (_i, [_p, _i, C.c_double, _i, _p, _p, _i, _dp]),
+        "sfm_cfl_dt": (_i, [_p, _i, _dp, _dp]),
+        "sfm_last_launches": (_i, [_p, _ip]),
+        "sfm_debug_set": (_i, [_p, _i, C.c_longlong]),
+        "sfm_set_model": (_i, [_p, _i, _i, _i, C.c_double, _dp, _i, _ip, _i, _ip, _i, _ip]),
+        "sfm_build_roms": (_i, [_p, _ip, _ip, C.c_double, C.c_double,
+                                C.POINTER(sfm_build_report)]),
+        "sfm_project_sources": (_i, [_p, _i, _dp, C.c_double]),
+        "sfm_project_receivers": (_i, [_p, _i, _dp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(h, rc):
+    if rc != SFM_OK:
+        msg = _lib.sfm_last_error(h)
+        raise SfmError(rc, msg.decode() if msg else "")
+
+
+def _iarr(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(_ip)
+
+
+def _darr(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_dp)
+
+
+def sfm_create(device=0):
+    lib = load()
+    h = _p()
+    rc = lib.sfm_create(C.byref(h), int(device))
+    _check(None, rc)
+    return h
+
+
+def sfm_destroy(h):
+    load().sfm_destroy(h)
+
+
+def sfm_last_error(h):
+    return load().sfm_last_error(h).decode()
+
+
+def sfm_set_stream(h, stream_ptr):
+    _check(h, load().sfm_set_stream(h, _p(int(stream_ptr)) if stream_ptr else None))
+
+
+def sfm_set_topology(h, k_sub, m_face, nbr):
+    k, kp = _iarr(k_sub)
+    m, mp = _iarr(np.asarray(m_face).reshape(-1))
+    n, np_ = _iarr(np.asarray(nbr).reshape(-1))
+    _check(h, load().sfm_set_topology(h, len(k), kp, mp, np_))
+
+
+def sfm_set_coeffs(h, coeffs):
+    c, cp = _darr(np.asarray(coeffs).reshape(-1))
+    _check(h, load().sfm_set_coeffs(h, cp, c.size))
+
+
+def sfm_get_coeffs(h):
+    need = C.c_size_t(0)
+    _check(h, load().sfm_get_coeffs(h, None, 0, C.byref(need)))
+    out = np.empty(need.value, dtype=np.float64)
+    _check(h, load().sfm_get_coeffs(h, out.ctypes.data_as(_dp), out.size, C.byref(need)))
+    return out
+
+
+def sfm_set_sources(h, nshots, pair_shot, pair_sub, rows):
+    a, ap = _iarr(pair_shot)
+    b, bp = _iarr(pair_sub)
+    r, rp = _darr(np.asarray(rows).reshape(-1))
+    _check(h, load().sfm_set_sources(h, int(nshots), len(a), ap, bp, rp))
+
+
+def sfm_set_receivers(h, nrec, pair_rec, pair_sub, rows):
+    a, ap = _iarr(pair_rec)
+    b, bp = _iarr(pair_sub)
+    r, rp = _darr(np.asarray(rows).reshape(-1))
+    _check(h, load().sfm_set_receivers(h, int(nrec), len(a), ap, bp, rp))
+
+
+def sfm_run(h, precision, dt, nsteps, wavelet, nshots, nrec, traces=None, device_ptrs=None):
+    """Step the coupled ROMs.  Host form: ``wavelet`` is a [nshots, nsteps]
+    array and the traces [nshots, nrec, nsteps+1] are returned.  Device form:
+    ``device_ptrs=(wavelet_ptr, traces_ptr)`` (FP64 device buffers).
+    Returns ``(traces, kernel_ms)``."""
+    ms = C.c_double(0.0)
+    if device_ptrs is not None:
+        wp, tp = device_ptrs
+        _check(h, load().sfm_run(h, int(precision), float(dt), int(nsteps), _p(int(wp)),
+                                 _p(int(tp)), SFM_DEVICE_PTR, C.byref(ms)))
+        return None, ms.value
+    w, _ = _darr(np.asarray(wavelet).reshape(nshots, nsteps))
+    out = np.empty((nshots, nrec, nsteps + 1)) if traces is None else traces
+    _check(h, load().sfm_run(h, int(precision), float(dt), int(nsteps),
+                             _p(w.ctypes.data), _p(out.ctypes.data), 0, C.byref(ms)))
+    return out, ms.value
+
+
+def sfm_cfl_dt(h, iters=300):
+    lam = C.c_double(0.0)
+    dt = C.c_double(0.0)
+    _check(h, load().sfm_cfl_dt(h, int(iters), C.byref(lam), C.byref(dt)))
+    return lam.value, dt.value
+
+
+def sfm_last_launches(h):
+    n = C.c_int(0)
+    _check(h, load().sfm_last_launches(h, C.byref(n)))
+    return n.value
+
+
+def sfm_debug_set(h, key, value):
+    _check(h, load().sfm_debug_set(h, int(key), int(value)))
+
+
+def sfm_set_model(h, c, hgrid, xcuts, ycuts, zcuts):
+    """``c``: [nz, ny, nx] cell velocities; cuts: node indices 0..n per axis."""
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    nz, ny, nx = c.shape
+    x, xp = _iarr(xcuts)
+    y, yp = _iarr(ycuts)
+    z, zp = _iarr(zcuts)
+    _check(h, load().sfm_set_model(h, nx, ny, nz, float(hgrid), c.ctypes.data_as(_dp),
+                                   len(x) - 1, xp, len(y) - 1, yp, len(z) - 1, zp))
+
+
+def sfm_build_roms(h, m_sub, k_sub, sigma, cg_tol=1e-14):
+    m, mp = _iarr(m_sub)
+    k, kp = _iarr(k_sub)
+    rep = sfm_build_report()
+    _check(h, load().sfm_build_roms(h, mp, kp, float(sigma), float(cg_tol), C.byref(rep)))
+    return {f: getattr(rep, f) for f, _ in sfm_build_report._fields_}
+
+
+def sfm_project_sources(h, xyz, width):
+    x, xp = _darr(np.asarray(xyz).reshape(-1, 3))
+    _check(h, load().sfm_project_sources(h, x.shape[0], xp, float(width)))
+
+
+def sfm_project_receivers(h, xyz):
+    x, xp = _darr(np.asarray(xyz).reshape(-1, 3))
+    _check(h, load().sfm_project_receivers(h, x.shape[0], xp))

@@ -280,9 +280,11 @@ def uneven_cuts(n, rng, choices=(16, 20, 24, 32)):
 # the workloads
 # ----------------------------------------------------------------------------
 
-def default_sigma(f_peak):
-    """Default Krylov shift ``(2 pi f_peak / 10)^2``."""
-    return (2.0 * np.pi * f_peak / 10.0) ** 2
+def default_sigma(f_peak, factor=2.5):
+    """Krylov shift ``(2 pi factor f_peak)^2``: the source band's upper edge by
+    default (factor 2.5).  Deep ROMs (k >= 16) use a larger factor so that
+    their S-fraction coefficients stay representable."""
+    return (2.0 * np.pi * factor * f_peak) ** 2
 
 
 def config1():
@@ -309,7 +311,7 @@ def config2(seed=SEED):
     xs = np.linspace(0.0, n * h, 1024)
     rec = np.stack([xs, np.full(1024, 96 * h), np.zeros(1024)], axis=1)
     return Problem("cfg2_192c_8x8x8_m8_k16", n, n, n, h, c, cuts, cuts.copy(), cuts.copy(),
-                   np.full(512, 8), np.full(512, 16), default_sigma(20.0), 20.0,
+                   np.full(512, 8), np.full(512, 16), default_sigma(20.0, 8.0), 20.0,
                    np.array([[96 * h, 96 * h, 8 * h]]), rec, 4000)
 
 
@@ -332,7 +334,7 @@ def config3(seed=SEED):
     rx, ry = np.meshgrid(r, r, indexing="ij")
     rec = np.stack([rx.ravel(), ry.ravel(), np.zeros(256)], axis=1)
     return Problem("cfg3_256x256x128_uneven_64shots", nx, ny, nz, h, c, xc, yc, zc, m, k,
-                   default_sigma(20.0), 20.0, src, rec, 3000)
+                   default_sigma(20.0, 8.0), 20.0, src, rec, 3000)
 
 
 def config5(seed=SEED):
@@ -351,7 +353,7 @@ def config5(seed=SEED):
     qx, qy = np.meshgrid(rx, ry, indexing="ij")
     rec = np.stack([qx.ravel(), qy.ravel(), np.zeros(512)], axis=1)
     return Problem("cfg5_512x512x256_32c_128shots", nx, ny, nz, h, c, xc, yc, zc,
-                   np.full(2048, 8), np.full(2048, 24), default_sigma(20.0), 20.0,
+                   np.full(2048, 8), np.full(2048, 24), default_sigma(20.0, 8.0), 20.0,
                    src, rec, 6000)
 
 

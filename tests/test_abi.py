@@ -1,0 +1,48 @@
+"""The C-ABI library builds, loads and exports every symbol ``include/sfm.h``
+declares (no compute calls: this runs without a GPU)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1406_6923_gb300 import _build, sfm
+    if not os.path.exists(sfm.LIB_PATH):
+        _build.build()
+    return sfm.load()
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "sfm.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(sfm_[a-z_]+)\s*\(", txt)))
+
+
+def test_header_declares_what_the_binding_lists():
+    from paper_1406_6923_gb300 import sfm
+    assert _declared() == sorted(sfm.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_last_error_without_handle_is_callable(lib):
+    assert isinstance(lib.sfm_last_error(None), bytes)
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    import importlib
+    from paper_1406_6923_gb300 import sfm
+    saved = sfm._lib
+    try:
+        sfm._lib = None
+        with pytest.raises(ImportError):
+            sfm.load(str(tmp_path / "missing.so"))
+    finally:
+        sfm._lib = saved
