@@ -237,6 +237,7 @@ def main():
     sfm.sfm_project_sources(h, p.src_xyz, p.src_width)
     sfm.sfm_project_receivers(h, p.rec_xyz)
     lam, dtc = sfm.sfm_cfl_dt(h, 1000)
+    sfm.sfm_free_build(h)              # the Krylov bases are not needed any more
     build_s = time.perf_counter() - t0
     dt = p.dt_safety * dtc
     dtf = fine_dt(p)
@@ -314,7 +315,6 @@ def main():
     # roofline of the persistent stepping kernel
     pk, pk_kind = peaks()
     word = {"fp32": 4, "fp32x2": 8, "fp64": 8}[chosen]
-    nrpairs = int(getattr(h, "nrpairs", 0) or 0)
     bytes_step = algorithmic_bytes_per_step(p.nsub, 48, 16, 8, count_rpairs(sfm, h, p), word)
     kms = statistics.mean(kern_ms)
     achieved = bytes_step * nsteps / (kms * 1e-3) / 1e9

@@ -149,9 +149,11 @@ int sfm_run(sfm_handle* h, int precision, double dt, int nsteps, const double* w
             double* traces, int flags, double* kernel_ms);
 
 /*
- * Largest eigenvalue of the coupled ROM system's MM^{-1} KK (power
- * iteration with the FP64 stepping operator, `iters` iterations) and the
- * leapfrog limit dt_cfl = 2/sqrt(lambda_max).  Either output may be NULL.
+ * Largest eigenvalue of the coupled ROM system's MM^{-1} KK and the leapfrog
+ * limit dt_cfl = 2/sqrt(lambda_max): `iters` power iterations with the FP64
+ * stepping operator, reporting the Rayleigh quotient q^T KK q / q^T MM q in
+ * the MM inner product (a lower bound that converges quadratically).
+ * Either output may be NULL.
  */
 int sfm_cfl_dt(sfm_handle* h, int iters, double* lambda_max, double* dt_cfl);
 
@@ -213,6 +215,11 @@ int sfm_project_sources(sfm_handle* h, int nshots, const double* xyz, double wid
  * the value at a shared node being the mass-weighted mean over its copies.
  * Sets the receivers as sfm_set_receivers would. */
 int sfm_project_receivers(sfm_handle* h, int nrec, const double* xyz);
+
+/* Release the offline builder's per-subdomain bases (Krylov V, Lanczos
+ * basis, masses); the coefficients, sources and receivers already set stay.
+ * Projecting new points afterwards needs a new sfm_build_roms. */
+int sfm_free_build(sfm_handle* h);
 
 /* Number of device kernels launched by the last sfm_run. */
 int sfm_last_launches(const sfm_handle* h, int* launches);

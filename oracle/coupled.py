@@ -38,6 +38,8 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
+from .eig import lanczos_max
+
 
 class RomSet:
     """All subdomain ROMs of a problem in S-fraction form plus the projected
@@ -162,10 +164,10 @@ def step_structured(rs, dt, nsteps, wavelet):
     return out
 
 
-def lambda_max(rs, tol=1e-10):
-    """Largest eigenvalue of ``MM^{-1} KK`` without assembling KK: Lanczos
-    (ARPACK) on the symmetric ``C^T KK C``, ``C C^T = MM^{-1}`` blockwise, with
-    ``KK x`` evaluated subdomain by subdomain as ``E^T D^T Gamma D E x``."""
+def lambda_max(rs, tol=1e-12):
+    """Largest eigenvalue of ``MM^{-1} KK`` without assembling KK: Lanczos on
+    the symmetric ``C^T KK C``, ``C C^T = MM^{-1}`` blockwise, with ``KK x``
+    evaluated subdomain by subdomain as ``E^T D^T Gamma D E x``."""
     topo = rs.topo
     nfm = int(topo.face_off[-1])
     int_off = np.zeros(rs.nsub + 1, dtype=int)
@@ -199,8 +201,7 @@ def lambda_max(rs, tol=1e-10):
             np.add.at(y, E.ravel(), out.reshape(-1))
         return y
 
-    op = spla.LinearOperator((n, n), matvec=lambda v: C.T @ KK(C @ np.ravel(v)), dtype=np.float64)
-    return float(spla.eigsh(op, k=1, which="LA", tol=tol, return_eigenvectors=False)[0])
+    return lanczos_max(lambda v: C.T @ KK(C @ v), n, tol=tol)
 
 
 # ----------------------------------------------------------------------------
@@ -271,8 +272,7 @@ class Assembled:
         S = C.T @ self.KK @ C
         if self.n <= 3000:
             return float(np.linalg.eigvalsh(S.toarray())[-1])
-        return float(spla.eigsh(S, k=1, which="LA", tol=1e-10,
-                                return_eigenvectors=False)[0])
+        return lanczos_max(lambda v: S @ v, self.n)
 
     def cfl_dt(self):
         """Leapfrog limit ``2 / sqrt(lambda_max(MM^{-1} KK))``."""

@@ -22,6 +22,8 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
+from .eig import lanczos_max
+
 
 def box_shape(box):
     x0, x1, y0, y1, z0, z1 = box
@@ -113,7 +115,7 @@ def lambda_max(K, mass):
     L = symmetrised(K, mass)
     if L.shape[0] <= 400:
         return float(np.linalg.eigvalsh(L.toarray())[-1])
-    return float(spla.eigsh(L, k=1, which="LA", tol=1e-12, return_eigenvectors=False)[0])
+    return lanczos_max(lambda v: L @ v, L.shape[0])
 
 
 def cfl_dt(K, mass):

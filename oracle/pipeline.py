@@ -93,9 +93,9 @@ def build(problem, keep=False, subs=None):
     return rs
 
 
-def rom_dt(rs, safety=0.9):
+def rom_dt(rs, safety=0.9, tol=1e-9):
     """``safety * dt_CFL`` of the coupled ROM system (0.9 by default)."""
-    return safety * 2.0 / np.sqrt(coupled.lambda_max(rs))
+    return safety * 2.0 / np.sqrt(coupled.lambda_max(rs, tol=tol))
 
 
 # ----------------------------------------------------------------------------

@@ -697,6 +697,17 @@ static int project_points(sfm_handle* h, int npts, const double* xyz, int kind, 
     return SFM_OK;
 }
 
+extern "C" int sfm_free_build(sfm_handle* h) {
+    if (!h) return SFM_ERR_ARG;
+    BuildState* B = bstate(h);
+    if (B) {
+        cudaSetDevice(h->device);
+        cudaStreamSynchronize(h->stream);
+        free_classes(B);
+    }
+    return SFM_OK;
+}
+
 extern "C" int sfm_project_sources(sfm_handle* h, int nshots, const double* xyz, double width) {
     if (!h) return SFM_ERR_ARG;
     BuildState* B = bstate(h);

@@ -49,6 +49,13 @@ struct PolF64 {
     using C = double;   // value in registers / shared memory
     static constexpr int kind = 0;
     __device__ static C ld(const S* p) { return *p; }
+    // two consecutive elements in one 16-byte load (p 16-byte aligned)
+    __device__ static void ld2(const S* p, C& a, C& b) {
+        const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+        a = v.x;
+        b = v.y;
+    }
+    __device__ static C ldg(const S* p) { return __ldg(p); }
     __device__ static void st(S* p, C v) { *p = v; }
     __device__ static C add(C a, C b) { return a + b; }
     __device__ static C sub(C a, C b) { return a - b; }
@@ -70,6 +77,12 @@ struct PolF32 {
     using C = float;
     static constexpr int kind = 1;
     __device__ static C ld(const S* p) { return *p; }
+    __device__ static void ld2(const S* p, C& a, C& b) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+        a = v.x;
+        b = v.y;
+    }
+    __device__ static C ldg(const S* p) { return __ldg(p); }
     __device__ static void st(S* p, C v) { *p = v; }
     __device__ static C add(C a, C b) { return a + b; }
     __device__ static C sub(C a, C b) { return a - b; }
@@ -92,6 +105,15 @@ struct PolF32x2 {
     static constexpr int kind = 2;
     __device__ static C ld(const S* p) {
         const float2 v = *p;
+        return {v.x, v.y};
+    }
+    __device__ static void ld2(const S* p, C& a, C& b) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+        a = {v.x, v.y};
+        b = {v.z, v.w};
+    }
+    __device__ static C ldg(const S* p) {
+        const float2 v = __ldg(p);
         return {v.x, v.y};
     }
     __device__ static void st(S* p, C v) { *p = make_float2(v.hi, v.lo); }

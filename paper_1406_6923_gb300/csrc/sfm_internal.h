@@ -23,8 +23,8 @@ struct StepParams {
     int kmax, bmax;
     const int* sub_b;            // [nsub]
     const int* sub_k;            // [nsub]
-    const long long* coef_off;   // [nsub] -> Gamma_1..k, Gammahat_1..k (b*b each)
-    const T* coef;
+    const long long* coef_off;   // [nsub] -> per level j: Gamma_j tiles, Gammahat_j tiles
+    const T* coef;               // 8x8-tile packed upper triangles (see pack_tiles_kernel)
     const int* face_off;         // [nsub*7] start of face f inside the b-vector
     const int* nbr;              // [nsub*6]
     const long long* H_off;      // [nsub*6] -> m_f*m_f block, or -1
@@ -50,6 +50,8 @@ struct StepParams {
     int* err;                    // device error word (0 = ok)
     unsigned long long timeout_ns;
     int skip_arrive;             // test hook: this block skips its barrier arrival (-1: none)
+    T* Kx;                       // optional: receives -KK U (the flux sums before the mass
+                                 // blocks are applied), state layout; NULL when stepping
 };
 
 // launchers (step.cu); P is a number policy of numeric.cuh
@@ -67,8 +69,23 @@ cudaError_t launch_face_H(const double* coef, const long long* gh1_off, const in
 template <class P>
 cudaError_t launch_convert(const double* in, typename P::S* out, size_t n, cudaStream_t st);
 
+// FP64 masters (per subdomain: Gamma_1..k then Gammahat_1..k, b x b row-major)
+// -> 8x8-tile packed blocks in the policy's storage type.
+template <class P>
+cudaError_t launch_pack_tiles(const double* master, const long long* master_off,
+                              const long long* tile_off, const int* sub_b, const int* sub_k,
+                              int nsub, typename P::S* out, cudaStream_t st);
+
+// number of 8x8 tiles kept of a b x b symmetric block (upper triangle of tiles)
+inline long long sym_tiles(int b) {
+    const long long nt = (b + 7) / 8;
+    return nt * (nt + 1) / 2;
+}
+
 // power-iteration helpers (FP64)
 cudaError_t launch_sumsq(const double* x, size_t n, double* out, cudaStream_t st);
+cudaError_t launch_wdot(const double* x, const double* y, const double* w, size_t n, double* out,
+                        cudaStream_t st);
 cudaError_t launch_scale(const double* x, double* y, size_t n, const double* sumsq,
                          cudaStream_t st);
 
@@ -95,14 +112,14 @@ struct sfm_handle {
     // topology (host copies)
     int nsub = 0;
     std::vector<int> k, b, mface, nbr, face_off;     // face_off: nsub*7
-    std::vector<long long> coef_off, H_off, state_off, mail_off;
-    long long ncoef = 0, nH = 0, nstate = 0, nmail = 0;
+    std::vector<long long> coef_off, H_off, state_off, mail_off, tcoef_off;
+    long long ncoef = 0, nH = 0, nstate = 0, nmail = 0, ntcoef = 0;
     int kmax = 0, bmax = 0;
 
     // device copies of the topology
     int *d_b = nullptr, *d_k = nullptr, *d_face_off = nullptr, *d_nbr = nullptr;
     long long *d_coef_off = nullptr, *d_H_off = nullptr, *d_state_off = nullptr,
-              *d_mail_off = nullptr;
+              *d_mail_off = nullptr, *d_tcoef_off = nullptr;
 
     // FP64 master data
     double* d_coef64 = nullptr;

@@ -121,15 +121,60 @@ __device__ void readout(const StepParams<typename P::S>& p, const typename P::S*
     }
 }
 
+// y = M x for a symmetric b x b block M stored as its upper triangle of 8x8
+// tiles (tile (I,J), J >= I, at index I*nt - I(I-1)/2 + (J-I), row-major
+// inside the tile); one warp per block.  Lane (r, q) accumulates row 8I+r
+// over columns 8J+2q, 8J+2q+1 of every tile column J: a stored tile is one
+// coalesced 16-byte load per lane, a tile below the diagonal is read
+// transposed from its stored mirror (the same warp just touched it, so it
+// comes from L1).  x and y are in shared memory, padded to 8*nt.
+constexpr int NTMAX = 8;   // b <= 64
+
+template <class P>
+__device__ __forceinline__ void warp_symv(const typename P::S* tiles, int nt,
+                                          const typename P::C* x, typename P::C* y) {
+    using C = typename P::C;
+    const int lane = threadIdx.x & 31, r = lane >> 2, q = lane & 3;
+    for (int I = 0; I < nt; ++I) {
+        C e0[NTMAX], e1[NTMAX];
+#pragma unroll
+        for (int J = 0; J < NTMAX; ++J) {
+            if (J < nt) {
+                if (J >= I) {
+                    P::ld2(tiles + (long long)(I * nt - I * (I - 1) / 2 + (J - I)) * 64 + r * 8 + 2 * q,
+                           e0[J], e1[J]);
+                } else {
+                    const typename P::S* t = tiles + (long long)(J * nt - J * (J - 1) / 2 + (I - J)) * 64;
+                    e0[J] = P::ldg(t + (2 * q) * 8 + r);
+                    e1[J] = P::ldg(t + (2 * q + 1) * 8 + r);
+                }
+            }
+        }
+        typename P::Acc acc = P::acc0();
+#pragma unroll
+        for (int J = 0; J < NTMAX; ++J) {
+            if (J < nt) {
+                P::fma(acc, e0[J], x[8 * J + 2 * q]);
+                P::fma(acc, e1[J], x[8 * J + 2 * q + 1]);
+            }
+        }
+        C v = P::get(acc);
+        v = P::add(v, P::shfl_xor(v, 1));
+        v = P::add(v, P::shfl_xor(v, 2));
+        if (q == 0) y[8 * I + r] = v;
+    }
+}
+
 template <class P>
 __global__ void __launch_bounds__(256) step_kernel(StepParams<typename P::S> p) {
     using S = typename P::S;
     using C = typename P::C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* sU = reinterpret_cast<C*>(smem_raw);              // (kmax+1)*bmax
-    C* sD = sU + (p.kmax + 1) * p.bmax;                  // kmax*bmax: Delta, then psi
-    C* sPhi = sD + p.kmax * p.bmax;                      // kmax*bmax
-    C* red = sPhi + p.kmax * p.bmax;                     // 32
+    const int bpm = ((p.bmax + 7) / 8) * 8;              // padded block width
+    C* sU = reinterpret_cast<C*>(smem_raw);              // (kmax+1)*bpm
+    C* sD = sU + (p.kmax + 1) * bpm;                     // kmax*bpm: Delta, then psi
+    C* sPhi = sD + p.kmax * bpm;                         // kmax*bpm: phi, then a
+    C* red = sPhi + p.kmax * bpm;                        // 32
     const C dt2 = P::from_d(p.dt2);
 
     for (int n = 0; n < p.nsteps; ++n) {
@@ -141,50 +186,51 @@ __global__ void __launch_bounds__(256) step_kernel(StepParams<typename P::S> p) 
         for (int u = blockIdx.x; u < p.nunits; u += gridDim.x) {
             const int q = u / p.nsub, s = u - q * p.nsub;
             const int b = p.sub_b[s], k = p.sub_k[s], kb = k * b;
+            const int nt = (b + 7) >> 3, bp = nt * 8;
+            const long long ltile = 2LL * (nt * (nt + 1) / 2) * 64;   // per level
             const long long so = q * p.state_stride + p.state_off[s];
             const S* Uc = Ucur + so;
             S* Un = Unxt + so;
             S* dU = p.dU + so;
-            const S* G = p.coef + p.coef_off[s];            // Gamma_j at G + j*b*b
-            const S* Gh = G + (long long)k * b * b;          // Gammahat_j at Gh + j*b*b
+            const S* T0 = p.coef + p.coef_off[s];   // level j: Gamma_j at T0 + j*ltile,
+                                                    // Gammahat_j at T0 + j*ltile + ltile/2
             const long long sof = p.src_off[(long long)q * p.nsub + s];
             const C w = P::ld(p.wavelet + (long long)q * p.nsteps + n);
+            const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
             __syncthreads();
-            for (int t = threadIdx.x; t < kb; t += blockDim.x) sU[t] = P::ld(Uc + t);
-            for (int t = threadIdx.x; t < b; t += blockDim.x) sU[kb + t] = P::zero();
-            __syncthreads();
-            for (int t = threadIdx.x; t < kb; t += blockDim.x) sD[t] = P::sub(sU[t + b], sU[t]);
-            __syncthreads();
-            // phi_j = Gamma_j Delta_j, j = 1..k  (Gamma symmetric: column-major = row-major)
-            for (int t = threadIdx.x; t < kb; t += blockDim.x) {
-                const int j = t / b, i = t - j * b;
-                const S* Gj = G + (long long)j * b * b + i;
-                const C* dj = sD + j * b;
-                typename P::Acc acc = P::acc0();
-#pragma unroll 8
-                for (int c = 0; c < b; ++c) P::fma(acc, P::ld(Gj + (long long)c * b), dj[c]);
-                sPhi[t] = P::get(acc);
+            // padded copies: level j occupies [j*bp, j*bp + b), zeros up to bp
+            for (int t = threadIdx.x; t < (k + 1) * bp; t += blockDim.x) {
+                const int j = t / bp, i = t - j * bp;
+                sU[t] = (j < k && i < b) ? P::ld(Uc + j * b + i) : P::zero();
             }
+            __syncthreads();
+            for (int t = threadIdx.x; t < k * bp; t += blockDim.x) sD[t] = P::sub(sU[t + bp], sU[t]);
+            __syncthreads();
+            // phi_j = Gamma_j Delta_j, j = 1..k: one warp per level
+            for (int j = warp; j < k; j += nwarp)
+                warp_symv<P>(T0 + (long long)j * ltile, nt, sD + j * bp, sPhi + j * bp);
             __syncthreads();
             // (2.1) publish face data; psi_j for the interior levels
             S* my_mail = mail + q * p.mail_stride + p.mail_off[s];
             for (int t = threadIdx.x; t < kb; t += blockDim.x) {
+                const int j = t / b, i = t - j * b;
                 const C srcv = (sof >= 0) ? P::mul(P::ld(p.src + sof + t), w) : P::zero();
-                if (t < b) P::st(my_mail + t, P::add(sPhi[t], srcv));
-                else sD[t] = P::add(P::sub(sPhi[t], sPhi[t - b]), srcv);
+                if (j == 0) P::st(my_mail + i, P::add(sPhi[i], srcv));
+                else sD[j * bp + i] = P::add(P::sub(sPhi[j * bp + i], sPhi[(j - 1) * bp + i]), srcv);
             }
             __syncthreads();
-            // (2.2) interior update, Eq. (19)
+            // (2.2) a_j = Gammahat_j psi_j for j >= 2 (into sPhi), Eq. (19)
+            for (int j = 1 + warp; j < k; j += nwarp)
+                warp_symv<P>(T0 + (long long)j * ltile + ltile / 2, nt, sD + j * bp, sPhi + j * bp);
+            __syncthreads();
+            if (p.Kx)
+                for (int t = b + threadIdx.x; t < kb; t += blockDim.x)
+                    P::st(p.Kx + so + t, sD[(t / b) * bp + (t % b)]);
             for (int t = b + threadIdx.x; t < kb; t += blockDim.x) {
                 const int j = t / b, i = t - j * b;
-                const S* Ghj = Gh + (long long)j * b * b + i;
-                const C* pj = sD + j * b;
-                typename P::Acc acc = P::acc0();
-#pragma unroll 8
-                for (int c = 0; c < b; ++c) P::fma(acc, P::ld(Ghj + (long long)c * b), pj[c]);
-                const C d = P::add(P::ld(dU + t), P::mul(dt2, P::get(acc)));
+                const C d = P::add(P::ld(dU + t), P::mul(dt2, sPhi[j * bp + i]));
                 P::st(dU + t, d);
-                P::st(Un + t, P::add(sU[t], d));
+                P::st(Un + t, P::add(sU[j * bp + i], d));
             }
         }
 
@@ -212,6 +258,7 @@ __global__ void __launch_bounds__(256) step_kernel(StepParams<typename P::S> p) 
                     v = (nb < s) ? P::add(o, v) : P::add(v, o);
                 }
                 sD[t] = v;
+                if (p.Kx) P::st(p.Kx + so + t, v);
             }
             __syncthreads();
             for (int t = threadIdx.x; t < b; t += blockDim.x) {
@@ -240,8 +287,8 @@ __global__ void __launch_bounds__(256) step_kernel(StepParams<typename P::S> p) 
 template <class P>
 size_t step_smem_bytes(int kmax, int bmax, int block) {
     (void)block;
-    return sizeof(typename P::C) *
-           ((size_t)(kmax + 1) * bmax + 2 * (size_t)kmax * bmax + 32);
+    const size_t bp = (size_t)((bmax + 7) / 8) * 8;
+    return sizeof(typename P::C) * ((size_t)(kmax + 1) * bp + 2 * (size_t)kmax * bp + 32);
 }
 
 template <class P>
@@ -328,10 +375,51 @@ cudaError_t launch_convert(const double* in, typename P::S* out, size_t n, cudaS
     return cudaGetLastError();
 }
 
+template <class P>
+__global__ void pack_tiles_kernel(const double* master, const long long* master_off,
+                                  const long long* tile_off, const int* sub_b, const int* sub_k,
+                                  typename P::S* out) {
+    const int s = blockIdx.y;
+    const int b = sub_b[s], k = sub_k[s];
+    const int nt = (b + 7) / 8, T = nt * (nt + 1) / 2;
+    const long long total = 2LL * k * T * 64;
+    const double* m = master + master_off[s];
+    typename P::S* o = out + tile_off[s];
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int rc = (int)(e & 63);
+        long long rest = e >> 6;
+        const int tix = (int)(rest % T);
+        rest /= T;
+        const int which = (int)(rest & 1), j = (int)(rest >> 1);
+        int I = 0, base = 0;
+        while (base + (nt - I) <= tix) { base += nt - I; ++I; }
+        const int J = I + (tix - base);
+        const int row = 8 * I + (rc >> 3), col = 8 * J + (rc & 7);
+        double v = 0.0;
+        if (row < b && col < b) v = m[((long long)which * k + j) * b * b + (long long)row * b + col];
+        P::st(o + e, P::from_d(v));
+    }
+}
+
+template <class P>
+cudaError_t launch_pack_tiles(const double* master, const long long* master_off,
+                              const long long* tile_off, const int* sub_b, const int* sub_k,
+                              int nsub, typename P::S* out, cudaStream_t st) {
+    for (int s0 = 0; s0 < nsub; s0 += 65535) {
+        const int ns = nsub - s0 < 65535 ? nsub - s0 : 65535;
+        pack_tiles_kernel<P><<<dim3(64, ns), 256, 0, st>>>(master, master_off + s0, tile_off + s0,
+                                                          sub_b + s0, sub_k + s0, out);
+    }
+    return cudaGetLastError();
+}
+
 #define SFM_INST2(P)                                                                           \
     template cudaError_t launch_reduce_traces<P>(const P::S*, const int*, const int*, int, int, \
                                                  int, int, double*, int*, cudaStream_t);       \
-    template cudaError_t launch_convert<P>(const double*, P::S*, size_t, cudaStream_t);
+    template cudaError_t launch_convert<P>(const double*, P::S*, size_t, cudaStream_t);        \
+    template cudaError_t launch_pack_tiles<P>(const double*, const long long*, const long long*, \
+                                              const int*, const int*, int, P::S*, cudaStream_t);
 SFM_INST2(PolF64)
 SFM_INST2(PolF32)
 SFM_INST2(PolF32x2)
@@ -353,6 +441,21 @@ __global__ void scale_kernel(const double* x, double* y, size_t n, const double*
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x)
         y[i] = x[i] * s;
+}
+
+__global__ void wdot_kernel(const double* x, const double* y, const double* w, size_t n,
+                            double* out) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (size_t i = threadIdx.x; i < n; i += blockDim.x) acc += w[i] * x[i] * y[i];
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) *out = acc;
+}
+
+cudaError_t launch_wdot(const double* x, const double* y, const double* w, size_t n, double* out,
+                        cudaStream_t st) {
+    wdot_kernel<<<1, 1024, 0, st>>>(x, y, w, n, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_sumsq(const double* x, size_t n, double* out, cudaStream_t st) {

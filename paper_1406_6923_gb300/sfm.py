@@ -34,7 +34,7 @@ SFM_DEVICE_PTR = 1
 EXPORTS = ["sfm_create", "sfm_destroy", "sfm_last_error", "sfm_set_stream", "sfm_set_topology",
            "sfm_set_coeffs", "sfm_get_coeffs", "sfm_set_sources", "sfm_set_receivers",
            "sfm_run", "sfm_cfl_dt", "sfm_last_launches", "sfm_debug_set", "sfm_set_model",
-           "sfm_build_roms", "sfm_project_sources", "sfm_project_receivers"]
+           "sfm_build_roms", "sfm_project_sources", "sfm_project_receivers", "sfm_free_build"]
 
 
 class sfm_build_report(C.Structure):
@@ -84,6 +84,7 @@ def load(path=LIB_PATH):
                                 C.POINTER(sfm_build_report)]),
         "sfm_project_sources": (_i, [_p, _i, _dp, C.c_double]),
         "sfm_project_receivers": (_i, [_p, _i, _dp]),
+        "sfm_free_build": (_i, [_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -225,3 +226,7 @@ def sfm_project_sources(h, xyz, width):
 def sfm_project_receivers(h, xyz):
     x, xp = _darr(np.asarray(xyz).reshape(-1, 3))
     _check(h, load().sfm_project_receivers(h, x.shape[0], xp))
+
+
+def sfm_free_build(h):
+    _check(h, load().sfm_free_build(h))

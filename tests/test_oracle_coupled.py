@@ -132,3 +132,17 @@ def test_rom_converges_to_the_slit_fine_grid():
         errs.append(pipeline.rel_l2(di, ref))
     assert all(a > b for a, b in zip(errs, errs[1:])), errs
     assert errs[-1] < 1e-2, errs
+
+
+def test_lanczos_max_matches_dense_eigvalsh():
+    """The stability limits use a Lanczos iteration; pin it to LAPACK's
+    dense eigenvalues on the assembled ROM system and a random SPD matrix."""
+    from oracle.eig import lanczos_max
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((300, 300))
+    A = X @ X.T
+    assert abs(lanczos_max(lambda v: A @ v, 300) / np.linalg.eigvalsh(A)[-1] - 1) < 1e-10
+    p = inputs.small_problem(ncell=(8, 8, 8), cuts=(4, 4, 4), m=4, k=3, model="random")
+    rs = pipeline.build(p)
+    A = coupled.Assembled(rs)
+    assert abs(coupled.lambda_max(rs) / A.lambda_max() - 1) < 1e-10
