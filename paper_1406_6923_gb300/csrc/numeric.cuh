@@ -56,6 +56,7 @@ struct PolF64 {
         b = v.y;
     }
     __device__ static C ldg(const S* p) { return __ldg(p); }
+    __device__ static void ld2p(const S* p, C& a, C& b) { const double2 v = *reinterpret_cast<const double2*>(p); a = v.x; b = v.y; }
     __device__ static void st(S* p, C v) { *p = v; }
     __device__ static C add(C a, C b) { return a + b; }
     __device__ static C sub(C a, C b) { return a - b; }
@@ -69,6 +70,7 @@ struct PolF64 {
     };
     __device__ static Acc acc0() { return {0.0}; }
     __device__ static void fma(Acc& a, C x, C y) { a.s = ::fma(x, y, a.s); }
+    __device__ static Acc merge(const Acc& a, const Acc& b) { return {a.s + b.s}; }
     __device__ static C get(const Acc& a) { return a.s; }
 };
 
@@ -83,6 +85,7 @@ struct PolF32 {
         b = v.y;
     }
     __device__ static C ldg(const S* p) { return __ldg(p); }
+    __device__ static void ld2p(const S* p, C& a, C& b) { const float2 v = *reinterpret_cast<const float2*>(p); a = v.x; b = v.y; }
     __device__ static void st(S* p, C v) { *p = v; }
     __device__ static C add(C a, C b) { return a + b; }
     __device__ static C sub(C a, C b) { return a - b; }
@@ -96,6 +99,7 @@ struct PolF32 {
     };
     __device__ static Acc acc0() { return {0.f}; }
     __device__ static void fma(Acc& a, C x, C y) { a.s = fmaf(x, y, a.s); }
+    __device__ static Acc merge(const Acc& a, const Acc& b) { return {a.s + b.s}; }
     __device__ static C get(const Acc& a) { return a.s; }
 };
 
@@ -115,6 +119,11 @@ struct PolF32x2 {
     __device__ static C ldg(const S* p) {
         const float2 v = __ldg(p);
         return {v.x, v.y};
+    }
+    __device__ static void ld2p(const S* p, C& a, C& b) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        a = {v.x, v.y};
+        b = {v.z, v.w};
     }
     __device__ static void st(S* p, C v) { *p = make_float2(v.hi, v.lo); }
     __device__ static C add(C a, C b) { return df_add(a, b); }
@@ -136,12 +145,20 @@ struct PolF32x2 {
         float s, e;
     };
     __device__ static Acc acc0() { return {0.f, 0.f}; }
+    // The running sum s and the error e each advance by one addition per
+    // product; the two-sum error, the product error and the cross terms are
+    // formed off that chain.
     __device__ static void fma(Acc& a, C x, C y) {
         const float p = x.hi * y.hi;
         const float pe = fmaf(x.hi, y.hi, -p);
         const df t = two_sum(a.s, p);
+        const float c = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, t.lo + pe));
         a.s = t.hi;
-        a.e = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, a.e + (t.lo + pe)));
+        a.e = a.e + c;
+    }
+    __device__ static Acc merge(const Acc& a, const Acc& b) {
+        const df t = two_sum(a.s, b.s);
+        return {t.hi, (a.e + b.e) + t.lo};
     }
     __device__ static C get(const Acc& a) {
         const df t = two_sum(a.s, a.e);

@@ -77,7 +77,7 @@ cudaError_t launch_pack_tiles(const double* master, const long long* master_off,
                               int nsub, typename P::S* out, cudaStream_t st);
 
 // number of 8x8 tiles kept of a b x b symmetric block (upper triangle of tiles)
-inline long long sym_tiles(int b) {
+__host__ __device__ inline long long sym_tiles(int b) {
     const long long nt = (b + 7) / 8;
     return nt * (nt + 1) / 2;
 }

@@ -44,13 +44,79 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Bounded device-wide barrier.  Returns false (and sets *err) when the
-// barrier did not complete within timeout_ns, or when another block
-// reported an error; every block then leaves the kernel.
+// Block layout of the stepping kernel: NCW consumer warps do the arithmetic,
+// one producer warp streams the coefficient blocks into shared memory with
+// bulk asynchronous copies (the TMA engine) through a ring of NSTAGE stages.
+constexpr int NCW = 8;
+constexpr int NCT = NCW * 32;
+constexpr int STEP_BLOCK = NCT + 32;
+constexpr int NSTAGE = 6;
+
+__device__ __forceinline__ void cbar() {
+    asm volatile("bar.sync 1, %0;" ::"n"(NCT) : "memory");
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void* ptr) {
+    return (unsigned)__cvta_generic_to_shared(ptr);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for a phase of an mbarrier: false (with *err set) when it did
+// not complete within timeout_ns or another block reported an error.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int* err,
+                                          unsigned long long timeout_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*(volatile int*)err != 0) return false;
+        if (global_ns() - t0 > timeout_ns) {
+            atomicCAS(err, 0, (int)SFM_ERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Bounded device-wide barrier among the consumer threads of every block.
+// Returns false (and sets *err) when it did not complete within timeout_ns
+// or another block reported an error; every block then leaves the kernel.
 __device__ bool grid_barrier(unsigned int* bar, unsigned int target, int* err,
                              unsigned long long timeout_ns, int skip_arrive) {
     __shared__ int s_ok;
-    __syncthreads();
+    cbar();
     if (threadIdx.x == 0) {
         __threadfence();
         if ((int)blockIdx.x != skip_arrive) red_release_add_u32(bar, 1u);
@@ -67,7 +133,7 @@ __device__ bool grid_barrier(unsigned int* bar, unsigned int target, int* err,
         }
         s_ok = ok;
     }
-    __syncthreads();
+    cbar();
     return s_ok != 0;
 }
 
@@ -85,98 +151,160 @@ __device__ __forceinline__ T block_sum(T v, T* red) {
     return s;  // valid in thread 0
 }
 
-// Sum over the block in the policy's arithmetic (fixed order); valid in thread 0.
+// Sum over the consumer threads in the policy's arithmetic (fixed order);
+// valid in thread 0.
 template <class P>
 __device__ __forceinline__ typename P::C block_sum_p(typename P::C v, typename P::C* red) {
     for (int o = 16; o > 0; o >>= 1) v = P::add(v, P::shfl_xor(v, o));
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
+    cbar();
     if (lane == 0) red[wid] = v;
-    __syncthreads();
+    cbar();
     typename P::C s = P::zero();
     if (threadIdx.x == 0) {
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = P::add(s, red[w]);
+        for (int w = 0; w < NCW; ++w) s = P::add(s, red[w]);
     }
     return s;
 }
 
-// Receiver readout of U (buffer `Ubuf`) at sample n for this block's share of
-// (shot, pair) items.
+// Receiver readout of U (buffer `Ubuf`) at sample n.  Every (shot, pair)
+// item is one warp's compensated dot product of the pair's row with the
+// subdomain's state; items are spread over all consumer warps of the grid.
 template <class P>
-__device__ void readout(const StepParams<typename P::S>& p, const typename P::S* Ubuf, int n,
-                        typename P::C* red) {
+__device__ void readout(const StepParams<typename P::S>& p, const typename P::S* Ubuf, int n) {
     using C = typename P::C;
     const long long items = (long long)p.nshots * p.nrpairs;
-    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (long long it = (long long)blockIdx.x * NCW + warp; it < items;
+         it += (long long)gridDim.x * NCW) {
         const int q = (int)(it / p.nrpairs), r = (int)(it % p.nrpairs);
         const int s = p.rp_sub[r];
         const int kb = p.sub_k[s] * p.sub_b[s];
         const typename P::S* row = p.rrows + p.rp_off[r];
         const typename P::S* U = Ubuf + q * p.state_stride + p.state_off[s];
-        typename P::Acc acc = P::acc0();
-        for (int t = threadIdx.x; t < kb; t += blockDim.x) P::fma(acc, P::ld(row + t), P::ld(U + t));
-        const C v = block_sum_p<P>(P::get(acc), red);
-        if (threadIdx.x == 0)
-            P::st(p.partial + ((long long)q * (p.nsteps + 1) + n) * p.nrpairs + r, v);
+        typename P::Acc a0 = P::acc0(), a1 = P::acc0();
+        int t = lane;
+        for (; t + 32 < kb; t += 64) {
+            P::fma(a0, P::ld(row + t), P::ld(U + t));
+            P::fma(a1, P::ld(row + t + 32), P::ld(U + t + 32));
+        }
+        if (t < kb) P::fma(a0, P::ld(row + t), P::ld(U + t));
+        C v = P::get(P::merge(a0, a1));
+        for (int o = 16; o > 0; o >>= 1) v = P::add(v, P::shfl_xor(v, o));
+        if (lane == 0) P::st(p.partial + ((long long)q * (p.nsteps + 1) + n) * p.nrpairs + r, v);
     }
 }
 
-// y = M x for a symmetric b x b block M stored as its upper triangle of 8x8
-// tiles (tile (I,J), J >= I, at index I*nt - I(I-1)/2 + (J-I), row-major
-// inside the tile); one warp per block.  Lane (r, q) accumulates row 8I+r
-// over columns 8J+2q, 8J+2q+1 of every tile column J: a stored tile is one
-// coalesced 16-byte load per lane, a tile below the diagonal is read
-// transposed from its stored mirror (the same warp just touched it, so it
-// comes from L1).  x and y are in shared memory, padded to 8*nt.
-constexpr int NTMAX = 8;   // b <= 64
-
+// One tile row of y = M x for a symmetric block M held in shared memory as
+// its upper triangle of 8x8 tiles (tile (I,J), J >= I, at index
+// I*nt - I(I-1)/2 + (J-I), row-major inside the tile).  Lane (r, q) sums
+// row 8I+r over columns 8J+2q, 8J+2q+1 of every tile column J; a tile below
+// the diagonal is read transposed from its stored mirror.
 template <class P>
-__device__ __forceinline__ void warp_symv(const typename P::S* tiles, int nt,
-                                          const typename P::C* x, typename P::C* y) {
+__device__ __forceinline__ void tile_row(const typename P::S* tiles, int nt, int I,
+                                         const typename P::C* x, typename P::C* y) {
     using C = typename P::C;
     const int lane = threadIdx.x & 31, r = lane >> 2, q = lane & 3;
-    for (int I = 0; I < nt; ++I) {
-        C e0[NTMAX], e1[NTMAX];
-#pragma unroll
-        for (int J = 0; J < NTMAX; ++J) {
-            if (J < nt) {
-                if (J >= I) {
-                    P::ld2(tiles + (long long)(I * nt - I * (I - 1) / 2 + (J - I)) * 64 + r * 8 + 2 * q,
-                           e0[J], e1[J]);
-                } else {
-                    const typename P::S* t = tiles + (long long)(J * nt - J * (J - 1) / 2 + (I - J)) * 64;
-                    e0[J] = P::ldg(t + (2 * q) * 8 + r);
-                    e1[J] = P::ldg(t + (2 * q + 1) * 8 + r);
-                }
-            }
+    // two independent accumulators (even and odd tile columns) for ILP
+    typename P::Acc a0 = P::acc0(), a1 = P::acc0();
+    auto load = [&](int J, C& e0, C& e1) {
+        if (J >= I) {
+            P::ld2p(tiles + (I * nt - I * (I - 1) / 2 + (J - I)) * 64 + r * 8 + 2 * q, e0, e1);
+        } else {
+            const typename P::S* t = tiles + (J * nt - J * (J - 1) / 2 + (I - J)) * 64;
+            e0 = P::ld(t + (2 * q) * 8 + r);
+            e1 = P::ld(t + (2 * q + 1) * 8 + r);
         }
-        typename P::Acc acc = P::acc0();
-#pragma unroll
-        for (int J = 0; J < NTMAX; ++J) {
-            if (J < nt) {
-                P::fma(acc, e0[J], x[8 * J + 2 * q]);
-                P::fma(acc, e1[J], x[8 * J + 2 * q + 1]);
-            }
-        }
-        C v = P::get(acc);
-        v = P::add(v, P::shfl_xor(v, 1));
-        v = P::add(v, P::shfl_xor(v, 2));
-        if (q == 0) y[8 * I + r] = v;
+    };
+    int J = 0;
+    for (; J + 1 < nt; J += 2) {
+        C e0, e1, f0, f1;
+        load(J, e0, e1);
+        load(J + 1, f0, f1);
+        P::fma(a0, e0, x[8 * J + 2 * q]);
+        P::fma(a1, f0, x[8 * J + 8 + 2 * q]);
+        P::fma(a0, e1, x[8 * J + 2 * q + 1]);
+        P::fma(a1, f1, x[8 * J + 8 + 2 * q + 1]);
     }
+    if (J < nt) {
+        C e0, e1;
+        load(J, e0, e1);
+        P::fma(a0, e0, x[8 * J + 2 * q]);
+        P::fma(a0, e1, x[8 * J + 2 * q + 1]);
+    }
+    C v = P::get(P::merge(a0, a1));
+    v = P::add(v, P::shfl_xor(v, 1));
+    v = P::add(v, P::shfl_xor(v, 2));
+    if (q == 0) y[8 * I + r] = v;
+}
+
+// The coefficient blocks a block streams per (shot, subdomain) unit, in
+// order: Gamma_1..Gamma_k, then Gammahat_2..Gammahat_k.
+__device__ __forceinline__ long long unit_block_offset(long long T0, long long ltile, int m, int k) {
+    return (m < k) ? T0 + (long long)m * ltile : T0 + (long long)(m - k + 1) * ltile + ltile / 2;
 }
 
 template <class P>
-__global__ void __launch_bounds__(256) step_kernel(StepParams<typename P::S> p) {
+__global__ void __launch_bounds__(STEP_BLOCK) step_kernel(StepParams<typename P::S> p) {
     using S = typename P::S;
     using C = typename P::C;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int bpm = ((p.bmax + 7) / 8) * 8;              // padded block width
-    C* sU = reinterpret_cast<C*>(smem_raw);              // (kmax+1)*bpm
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int bpm = ((p.bmax + 7) / 8) * 8;
+    const int stage_elems = (int)(sym_tiles(p.bmax) * 64);
+    S* stages = reinterpret_cast<S*>(smem_raw);
+    C* sU = reinterpret_cast<C*>(stages + (size_t)NSTAGE * stage_elems);   // (kmax+1)*bpm
     C* sD = sU + (p.kmax + 1) * bpm;                     // kmax*bpm: Delta, then psi
     C* sPhi = sD + p.kmax * bpm;                         // kmax*bpm: phi, then a
     C* red = sPhi + p.kmax * bpm;                        // 32
-    const C dt2 = P::from_d(p.dt2);
+    unsigned long long* full = reinterpret_cast<unsigned long long*>(
+        (reinterpret_cast<uintptr_t>(red + 32) + 15) & ~(uintptr_t)15);
+    unsigned long long* empty = full + NSTAGE;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NSTAGE; ++i) {
+            mbar_init(full + i, 1);
+            mbar_init(empty + i, NCW);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == NCW) {
+        // ------------------------------ producer ------------------------------
+        if (lane != 0) return;
+        long long g = 0;
+        bool ok = true;
+        for (int n = 0; n < p.nsteps && ok; ++n) {
+            for (int u = blockIdx.x; u < p.nunits && ok; u += gridDim.x) {
+                const int s = u % p.nsub;
+                const int b = p.sub_b[s], k = p.sub_k[s];
+                const int nt = (b + 7) >> 3;
+                const long long ltile = 2LL * (nt * (nt + 1) / 2) * 64;
+                const unsigned bytes = (unsigned)((ltile / 2) * sizeof(S));
+                const long long T0 = p.coef_off[s];
+                for (int m = 0; m < 2 * k - 1; ++m, ++g) {
+                    const int st = (int)(g % NSTAGE);
+                    if (g >= NSTAGE &&
+                        !mbar_wait(empty + st, (unsigned)((g / NSTAGE - 1) & 1), p.err, p.timeout_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(full + st, bytes);
+                    bulk_g2s(stages + (size_t)st * stage_elems,
+                             p.coef + unit_block_offset(T0, ltile, m, k), bytes, full + st);
+                }
+            }
+        }
+        // never leave with copies in flight: wait for every issued stage
+        for (long long h = (g > NSTAGE ? g - NSTAGE : 0); h < g; ++h)
+            mbar_wait(full + (int)(h % NSTAGE), (unsigned)((h / NSTAGE) & 1), p.err, p.timeout_ns);
+        return;
+    }
+
+    // ------------------------------- consumers --------------------------------
+    const C dt2 = P::from_d(p.dt2);
+    long long g = 0;   // running index of the streamed blocks (same order as the producer)
     for (int n = 0; n < p.nsteps; ++n) {
         const S* Ucur = p.U[n % 3];
         S* Unxt = p.U[(n + 1) % 3];
@@ -187,46 +315,61 @@ __global__ void __launch_bounds__(256) step_kernel(StepParams<typename P::S> p) 
             const int q = u / p.nsub, s = u - q * p.nsub;
             const int b = p.sub_b[s], k = p.sub_k[s], kb = k * b;
             const int nt = (b + 7) >> 3, bp = nt * 8;
-            const long long ltile = 2LL * (nt * (nt + 1) / 2) * 64;   // per level
             const long long so = q * p.state_stride + p.state_off[s];
             const S* Uc = Ucur + so;
             S* Un = Unxt + so;
             S* dU = p.dU + so;
-            const S* T0 = p.coef + p.coef_off[s];   // level j: Gamma_j at T0 + j*ltile,
-                                                    // Gammahat_j at T0 + j*ltile + ltile/2
             const long long sof = p.src_off[(long long)q * p.nsub + s];
             const C w = P::ld(p.wavelet + (long long)q * p.nsteps + n);
-            const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-            __syncthreads();
+            cbar();
             // padded copies: level j occupies [j*bp, j*bp + b), zeros up to bp
-            for (int t = threadIdx.x; t < (k + 1) * bp; t += blockDim.x) {
+            for (int t = threadIdx.x; t < (k + 1) * bp; t += NCT) {
                 const int j = t / bp, i = t - j * bp;
                 sU[t] = (j < k && i < b) ? P::ld(Uc + j * b + i) : P::zero();
             }
-            __syncthreads();
-            for (int t = threadIdx.x; t < k * bp; t += blockDim.x) sD[t] = P::sub(sU[t + bp], sU[t]);
-            __syncthreads();
-            // phi_j = Gamma_j Delta_j, j = 1..k: one warp per level
-            for (int j = warp; j < k; j += nwarp)
-                warp_symv<P>(T0 + (long long)j * ltile, nt, sD + j * bp, sPhi + j * bp);
-            __syncthreads();
-            // (2.1) publish face data; psi_j for the interior levels
-            S* my_mail = mail + q * p.mail_stride + p.mail_off[s];
-            for (int t = threadIdx.x; t < kb; t += blockDim.x) {
-                const int j = t / b, i = t - j * b;
-                const C srcv = (sof >= 0) ? P::mul(P::ld(p.src + sof + t), w) : P::zero();
-                if (j == 0) P::st(my_mail + i, P::add(sPhi[i], srcv));
-                else sD[j * bp + i] = P::add(P::sub(sPhi[j * bp + i], sPhi[(j - 1) * bp + i]), srcv);
+            cbar();
+            for (int t = threadIdx.x; t < k * bp; t += NCT) sD[t] = P::sub(sU[t + bp], sU[t]);
+            cbar();
+            // phi_j = Gamma_j Delta_j (blocks m = 0..k-1), then after psi,
+            // a_j = Gammahat_j psi_j (blocks m = k..2k-2, level j = m-k+1).
+            // Tile rows of the streamed blocks are handed to the warps round
+            // robin; each warp releases every block once it is done with it.
+            int task = 0;
+            for (int half = 0; half < 2; ++half) {
+                const int m0 = half ? k : 0, m1 = half ? 2 * k - 1 : k;
+                for (int m = m0; m < m1; ++m, ++g) {
+                    const int st = (int)(g % NSTAGE);
+                    const int j = half ? m - k + 1 : m;
+                    const int first = (warp - task % NCW + NCW) % NCW;   // my first tile row
+                    // every warp waits for the block before releasing it, so that
+                    // releases of a stage arrive in block order
+                    if (!mbar_wait(full + st, (unsigned)((g / NSTAGE) & 1), p.err, p.timeout_ns))
+                        return;
+                    for (int I = first; I < nt; I += NCW)
+                        tile_row<P>(stages + (size_t)st * stage_elems, nt, I, sD + j * bp,
+                                    sPhi + j * bp);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(empty + st);
+                    task += nt;
+                }
+                cbar();
+                if (half == 0) {
+                    // (2.1) publish face data; psi_j for the interior levels
+                    S* my_mail = mail + q * p.mail_stride + p.mail_off[s];
+                    for (int t = threadIdx.x; t < kb; t += NCT) {
+                        const int j = t / b, i = t - j * b;
+                        const C srcv = (sof >= 0) ? P::mul(P::ld(p.src + sof + t), w) : P::zero();
+                        if (j == 0) P::st(my_mail + i, P::add(sPhi[i], srcv));
+                        else sD[j * bp + i] = P::add(P::sub(sPhi[j * bp + i], sPhi[(j - 1) * bp + i]), srcv);
+                    }
+                    cbar();
+                }
             }
-            __syncthreads();
-            // (2.2) a_j = Gammahat_j psi_j for j >= 2 (into sPhi), Eq. (19)
-            for (int j = 1 + warp; j < k; j += nwarp)
-                warp_symv<P>(T0 + (long long)j * ltile + ltile / 2, nt, sD + j * bp, sPhi + j * bp);
-            __syncthreads();
+            // (2.2) interior update, Eq. (19)
             if (p.Kx)
-                for (int t = b + threadIdx.x; t < kb; t += blockDim.x)
+                for (int t = b + threadIdx.x; t < kb; t += NCT)
                     P::st(p.Kx + so + t, sD[(t / b) * bp + (t % b)]);
-            for (int t = b + threadIdx.x; t < kb; t += blockDim.x) {
+            for (int t = b + threadIdx.x; t < kb; t += NCT) {
                 const int j = t / b, i = t - j * b;
                 const C d = P::add(P::ld(dU + t), P::mul(dt2, sPhi[j * bp + i]));
                 P::st(dU + t, d);
@@ -245,9 +388,9 @@ __global__ void __launch_bounds__(256) step_kernel(StepParams<typename P::S> p) 
             const long long so = q * p.state_stride + p.state_off[s];
             const S* mine = mail + q * p.mail_stride + p.mail_off[s];
             const int* fo = p.face_off + s * 7;
-            __syncthreads();
+            cbar();
             // sum of both sides' face data, lower subdomain index first
-            for (int t = threadIdx.x; t < b; t += blockDim.x) {
+            for (int t = threadIdx.x; t < b; t += NCT) {
                 int f = 0;
                 while (t >= fo[f + 1]) ++f;
                 const int nb = p.nbr[s * 6 + f];
@@ -260,8 +403,8 @@ __global__ void __launch_bounds__(256) step_kernel(StepParams<typename P::S> p) 
                 sD[t] = v;
                 if (p.Kx) P::st(p.Kx + so + t, v);
             }
-            __syncthreads();
-            for (int t = threadIdx.x; t < b; t += blockDim.x) {
+            cbar();
+            for (int t = threadIdx.x; t < b; t += NCT) {
                 int f = 0;
                 while (t >= fo[f + 1]) ++f;
                 const int m = fo[f + 1] - fo[f], i = t - fo[f];
@@ -275,29 +418,33 @@ __global__ void __launch_bounds__(256) step_kernel(StepParams<typename P::S> p) 
             }
         }
         // receiver readout of U^n (complete since the barrier above)
-        readout<P>(p, Ucur, n, red);
+        readout<P>(p, Ucur, n);
     }
     // final readout of U^{nsteps}, after every face update of the last step
     if (!grid_barrier(p.bar, (unsigned)(p.nsteps + 1) * gridDim.x, p.err, p.timeout_ns,
                       p.skip_arrive))
         return;
-    readout<P>(p, p.U[p.nsteps % 3], p.nsteps, red);
+    readout<P>(p, p.U[p.nsteps % 3], p.nsteps);
 }
 
 template <class P>
 size_t step_smem_bytes(int kmax, int bmax, int block) {
     (void)block;
     const size_t bp = (size_t)((bmax + 7) / 8) * 8;
-    return sizeof(typename P::C) * ((size_t)(kmax + 1) * bp + 2 * (size_t)kmax * bp + 32);
+    size_t bytes = (size_t)NSTAGE * sym_tiles(bmax) * 64 * sizeof(typename P::S);
+    bytes += sizeof(typename P::C) * ((size_t)(kmax + 1) * bp + 2 * (size_t)kmax * bp + 32);
+    bytes = (bytes + 15) & ~(size_t)15;
+    return bytes + 2 * NSTAGE * sizeof(unsigned long long);
 }
 
 template <class P>
 int step_max_grid(int block, size_t smem, int* grid_out) {
+    (void)block;
     int per_sm = 0, nsm = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(step_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<P>, block, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<P>, STEP_BLOCK, smem);
     if (per_sm < 1) return -1;
     *grid_out = per_sm * nsm;
     return 0;
@@ -305,14 +452,15 @@ int step_max_grid(int block, size_t smem, int* grid_out) {
 
 template <class P>
 cudaError_t launch_step(const StepParams<typename P::S>& p, int block, int grid, cudaStream_t st) {
-    const size_t smem = step_smem_bytes<P>(p.kmax, p.bmax, block);
+    (void)block;
+    const size_t smem = step_smem_bytes<P>(p.kmax, p.bmax, STEP_BLOCK);
     cudaError_t e = cudaFuncSetAttribute(step_kernel<P>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     StepParams<typename P::S> pc = p;
     void* args[] = {&pc};
-    return cudaLaunchCooperativeKernel((void*)step_kernel<P>, dim3(grid), dim3(block), args, smem,
-                                       st);
+    return cudaLaunchCooperativeKernel((void*)step_kernel<P>, dim3(grid), dim3(STEP_BLOCK), args,
+                                       smem, st);
 }
 
 #define SFM_INST(P)                                                                             \
