@@ -221,6 +221,44 @@ int sfm_project_receivers(sfm_handle* h, int nrec, const double* xyz);
  * Projecting new points afterwards needs a new sfm_build_roms. */
 int sfm_free_build(sfm_handle* h);
 
+/*
+ * sfm_run_static - the FP64 coupled stepping of sfm_run without allocating
+ * any device memory.  (Not a step of the paper's method, which has no
+ * counterpart to it: it serves callers of this library that cannot allocate
+ * device memory at the time they step, e.g. an application or framework
+ * that owns the whole GPU through its own allocator and treats further
+ * cudaMalloc calls as errors, or a latency-critical loop that must not pay
+ * for the device-wide synchronisation of cudaMalloc/cudaFree.)
+ *
+ * All inputs and outputs belong to the caller.  Host arrays: k_sub, m_face,
+ * nbr (as sfm_set_topology), src_shot/src_sub and rec_id/rec_sub (as
+ * sfm_set_sources/sfm_set_receivers).  Device arrays on `device`: coeffs
+ * (the sfm_set_coeffs layout, FP64), src_rows and rec_rows (the
+ * sfm_set_sources/sfm_set_receivers row layouts, FP64), wavelet
+ * [nshots][nsteps] and the output traces [nshots][nrec][nsteps+1] (FP64).
+ * Work is enqueued on `stream` (a cudaStream_t, NULL for the legacy default
+ * stream) and the call returns when it is done.
+ *
+ * Scratch memory: one static device array of 64 MiB per GPU, held by every
+ * GPU that loads the library until the process exits; a problem whose
+ * layout tables, tile-packed coefficients, state and partial receiver sums
+ * need more returns SFM_ERR_ARG (sfm_last_error(NULL) gives the size
+ * needed) before touching the device.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call
+ * shares the one array and re-initialises what must start at zero, so calls
+ * that overlap on the GPU (two streams, two host threads) race and must be
+ * serialised by the caller.  No cudaMalloc, cudaFree or allocating library
+ * routine is called.
+ * Errors: SFM_ERR_ARG, SFM_ERR_CUDA, SFM_ERR_TIMEOUT, SFM_ERR_NOT_SPD,
+ * SFM_ERR_UNSTABLE, reported through sfm_last_error(NULL).
+ */
+int sfm_run_static(int device, void* stream, int nsub, const int* k_sub, const int* m_face,
+                   const int* nbr, const double* coeffs, int nshots, int nsrc_pairs,
+                   const int* src_shot, const int* src_sub, const double* src_rows, int nrec,
+                   int nrec_pairs, const int* rec_id, const int* rec_sub, const double* rec_rows,
+                   double dt, int nsteps, const double* wavelet, double* traces);
+
 /* Number of device kernels launched by the last sfm_run. */
 int sfm_last_launches(const sfm_handle* h, int* launches);
 

@@ -77,6 +77,10 @@ struct RunBufs {
 
 }  // namespace
 
+namespace sfm {
+void set_global_error(const std::string& msg) { g_err = msg; }
+}  // namespace sfm
+
 struct sfm_ext {
     Cache<float> c32;
     Cache<double> c64;

@@ -95,6 +95,7 @@ cudaError_t launch_reduce_traces(const typename P::S* partial, const int* rec_pt
                                  int nrpairs, double* traces, int* bad, cudaStream_t st);
 
 void free_build(sfm_handle* h);
+void set_global_error(const std::string& msg);   // text of sfm_last_error(NULL)
 int set_topology_internal(sfm_handle* h, int nsub, const int* k_sub, const int* m_face,
                           const int* nbr);
 int set_coeffs_device(sfm_handle* h, const double* d_coeffs);

@@ -34,7 +34,7 @@ SFM_DEVICE_PTR = 1
 EXPORTS = ["sfm_create", "sfm_destroy", "sfm_last_error", "sfm_set_stream", "sfm_set_topology",
            "sfm_set_coeffs", "sfm_get_coeffs", "sfm_set_sources", "sfm_set_receivers",
            "sfm_run", "sfm_cfl_dt", "sfm_last_launches", "sfm_debug_set", "sfm_set_model",
-           "sfm_build_roms", "sfm_project_sources", "sfm_project_receivers", "sfm_free_build"]
+           "sfm_build_roms", "sfm_project_sources", "sfm_project_receivers", "sfm_free_build", "sfm_run_static"]
 
 
 class sfm_build_report(C.Structure):
@@ -85,6 +85,8 @@ def load(path=LIB_PATH):
         "sfm_project_sources": (_i, [_p, _i, _dp, C.c_double]),
         "sfm_project_receivers": (_i, [_p, _i, _dp]),
         "sfm_free_build": (_i, [_p]),
+        "sfm_run_static": (_i, [_i, _p, _i, _ip, _ip, _ip, _p, _i, _i, _ip, _ip, _p, _i, _i, _ip,
+                                _ip, _p, C.c_double, _i, _p, _p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -230,3 +232,24 @@ def sfm_project_receivers(h, xyz):
 
 def sfm_free_build(h):
     _check(h, load().sfm_free_build(h))
+
+
+def sfm_run_static(device, stream_ptr, k_sub, m_face, nbr, coeffs_ptr, nshots, src_shot, src_sub,
+                   src_rows_ptr, nrec, rec_id, rec_sub, rec_rows_ptr, dt, nsteps, wavelet_ptr,
+                   traces_ptr):
+    """FP64 stepping with no device allocation: the ``*_ptr`` arguments are
+    device addresses owned by the caller; the topology and pair lists are
+    host arrays."""
+    k, kp = _iarr(k_sub)
+    m, mp = _iarr(np.asarray(m_face).reshape(-1))
+    n, np_ = _iarr(np.asarray(nbr).reshape(-1))
+    a, ap = _iarr(src_shot)
+    b, bp = _iarr(src_sub)
+    c, cp = _iarr(rec_id)
+    d, dp = _iarr(rec_sub)
+    rc = load().sfm_run_static(int(device), _p(int(stream_ptr)) if stream_ptr else None, len(k),
+                               kp, mp, np_, _p(int(coeffs_ptr)), int(nshots), len(a), ap, bp,
+                               _p(int(src_rows_ptr)), int(nrec), len(c), cp, dp,
+                               _p(int(rec_rows_ptr)), float(dt), int(nsteps), _p(int(wavelet_ptr)),
+                               _p(int(traces_ptr)))
+    _check(None, rc)
