@@ -269,6 +269,9 @@ def main():
     else:
         chosen = args.precision
     prec = modes[chosen]
+    # block shape of the stepping kernel, picked by the library's autotuner
+    # (zero-source probes, outside the timed region)
+    tune_ncw, tune_nst, tune_us = sfm.sfm_autotune(h, prec, 200)
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
     for _ in range(args.warmup):
@@ -344,7 +347,9 @@ def main():
                       "conservative_value": ncell * nsteps * nshots / (ms * 1e-3) * world,
                       "l2": "256 MB buffer written between timed iterations",
                       "parallelism": "replicas" if world > 1 else "single GPU",
-                      "offline_build_s": build_s, "build": rep},
+                      "offline_build_s": build_s, "build": rep,
+                      "block_shape": {"consumer_warps": tune_ncw, "ring_stages": tune_nst,
+                                      "probe_us_per_time_step": tune_us}},
            "roofline": roof, "cpu_baseline": cpu,
            "e2e": {"value": e2e_val, "unit": UNIT,
                    "h2d_bytes_per_step": int(host_w.nbytes), "d2h_bytes_per_step": int(host_tr.nbytes)},

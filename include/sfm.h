@@ -158,6 +158,21 @@ int sfm_run(sfm_handle* h, int precision, double dt, int nsteps, const double* w
 int sfm_cfl_dt(sfm_handle* h, int iters, double* lambda_max, double* dt_cfl);
 
 /*
+ * Shape search for the stepping kernel of `precision` on this handle (no
+ * counterpart in the paper, whose method fixes no launch shape).  Each
+ * candidate block shape - consumer warps in {2,4,6,8,12,16} times
+ * coefficient ring stages in {2,3,4,6,8}, those whose shared memory fits -
+ * steps the coupled system `nsteps` steps from a zero source twice; the
+ * fastest (step kernel alone, CUDA events) becomes the shape of later
+ * sfm_run calls in that precision.  Results do not depend on the shape:
+ * every shape sums in the same order.  Outputs: the chosen consumer warps,
+ * ring stages and microseconds per time step; any may be NULL.  Needs
+ * coefficients, sources and receivers.  Errors: as sfm_run.
+ */
+int sfm_autotune(sfm_handle* h, int precision, int nsteps, int* ncw, int* nstage,
+                 double* us_per_step);
+
+/*
  * ---------------------------------------------------------------------------
  * Offline stage on the GPU (Algorithm 1 stage 1, FP64)
  * ---------------------------------------------------------------------------
@@ -267,8 +282,11 @@ int sfm_last_launches(const sfm_handle* h, int* launches);
  *   key 1: device-wide barrier time limit in nanoseconds (default 2e9);
  *   key 2: index of a block that skips its barrier arrivals (-1 = none), so
  *          that every block's bounded wait runs out and sfm_run returns
- *          SFM_ERR_TIMEOUT with the context still usable.
- * Errors: SFM_ERR_ARG for an unknown key.
+ *          SFM_ERR_TIMEOUT with the context still usable;
+ *   key 3: consumer warps per stepping block (1..16), all precisions;
+ *   key 4: coefficient ring stages per stepping block (2..16), all
+ *          precisions (keys 3 and 4 override sfm_autotune's choice).
+ * Errors: SFM_ERR_ARG for an unknown key or a value out of range.
  */
 int sfm_debug_set(sfm_handle* h, int key, long long value);
 

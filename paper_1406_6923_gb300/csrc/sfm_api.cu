@@ -93,6 +93,12 @@ struct sfm_ext {
     int* d_bad = nullptr;
     unsigned long long timeout_ns = 2000000000ull;
     int skip_arrive = -1;
+    // stepping block shape per precision (FP64, FP32, FP32x2): consumer
+    // warps and coefficient ring stages; sfm_autotune overwrites these
+    int ncw[3] = {8, 8, 8}, nstage[3] = {4, 4, 4};
+    int* d_piece_ptr = nullptr;
+    int4* d_pieces = nullptr;
+    int piece_grid = -1, piece_units = -1;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
@@ -143,7 +149,7 @@ int sfm_destroy(sfm_handle* h) {
     if (x) {
         x->c32.release(); x->c64.release(); x->c2.release();
         x->r32.release(); x->r64.release(); x->r2.release();
-        dfree(x->d_traces); dfree(x->d_bad);
+        dfree(x->d_traces); dfree(x->d_bad); dfree(x->d_piece_ptr); dfree(x->d_pieces);
         if (x->ev0) cudaEventDestroy(x->ev0);
         if (x->ev1) cudaEventDestroy(x->ev1);
         delete x;
@@ -186,6 +192,7 @@ int sfm_set_topology(sfm_handle* h, int nsub, const int* k_sub, const int* m_fac
     if (nsub <= 0 || !k_sub || !m_face || !nbr)
         return fail(h, SFM_ERR_ARG, "sfm_set_topology: bad arguments");
     CK(h, cudaSetDevice(h->device));
+    ext(h)->piece_grid = -1;   // the per-block pieces follow k_sub
     for (int s = 0; s < nsub; ++s) {
         if (k_sub[s] < 1) return fail(h, SFM_ERR_ARG, "sfm_set_topology: k < 1");
         int b = 0;
@@ -389,6 +396,16 @@ int sfm_debug_set(sfm_handle* h, int key, long long value) {
     if (!h) return fail(nullptr, SFM_ERR_ARG, "NULL handle");
     if (key == 1) { ext(h)->timeout_ns = (unsigned long long)value; return SFM_OK; }
     if (key == 2) { ext(h)->skip_arrive = (int)value; return SFM_OK; }
+    if (key == 3) {
+        if (value < 1 || value > 16) return fail(h, SFM_ERR_ARG, "sfm_debug_set: consumer warps 1..16");
+        for (int i = 0; i < 3; ++i) ext(h)->ncw[i] = (int)value;
+        return SFM_OK;
+    }
+    if (key == 4) {
+        if (value < 2 || value > 16) return fail(h, SFM_ERR_ARG, "sfm_debug_set: ring stages 2..16");
+        for (int i = 0; i < 3; ++i) ext(h)->nstage[i] = (int)value;
+        return SFM_OK;
+    }
     return fail(h, SFM_ERR_ARG, "sfm_debug_set: unknown key");
 }
 
@@ -437,6 +454,40 @@ static int prepare(sfm_handle* h) {
     CK(h, sfm::launch_convert<P>(h->d_rrows64, c.rrows, (size_t)h->nrrow, st));
     CK(h, cudaStreamSynchronize(st));
     c.valid = true;
+    return SFM_OK;
+}
+
+static int prec_id(sfm::PolF64) { return SFM_FP64; }
+static int prec_id(sfm::PolF32) { return SFM_FP32; }
+static int prec_id(sfm::PolF32x2) { return SFM_FP32X2; }
+
+// Grid of the persistent stepping kernel (co-resident blocks for the
+// chosen shape, at most one per level of work) and the per-block pieces.
+template <class P>
+static int step_setup(sfm_handle* h, int nunits, sfm::StepParams<typename P::S>& p, int* grid_out) {
+    sfm_ext* x = ext(h);
+    const int id = prec_id(P{});
+    int gmax = 0;
+    if (sfm::step_max_grid<P>(x->ncw[id], sfm::step_smem_bytes<P>(h->kmax, h->bmax, x->nstage[id]),
+                              &gmax) != 0)
+        return fail(h, SFM_ERR_ARG, "stepping: subdomain blocks too large for shared memory");
+    long long levels = 0;
+    for (int u = 0; u < nunits; ++u) levels += h->k[u % h->nsub];
+    const int grid = (int)std::max(1LL, std::min<long long>(gmax, levels));
+    if (grid != x->piece_grid || nunits != x->piece_units) {
+        std::vector<int> ptr;
+        std::vector<int4> pieces;
+        sfm::build_pieces(nunits, h->nsub, h->k.data(), grid, ptr, pieces);
+        CK(h, upload(x->d_piece_ptr, ptr.data(), ptr.size(), h->stream));
+        CK(h, upload(x->d_pieces, pieces.data(), pieces.size(), h->stream));
+        x->piece_grid = grid;
+        x->piece_units = nunits;
+    }
+    p.ncw = x->ncw[id];
+    p.nstage = x->nstage[id];
+    p.piece_ptr = x->d_piece_ptr;
+    p.pieces = x->d_pieces;
+    *grid_out = grid;
     return SFM_OK;
 }
 
@@ -510,15 +561,11 @@ static int run_impl(sfm_handle* h, double dt, int nsteps, const double* wavelet,
     p.skip_arrive = x->skip_arrive;
     p.Kx = nullptr;
 
-    const int block = 256;
-    int gmax = 0;
-    if (sfm::step_max_grid<P>(block, sfm::step_smem_bytes<P>(h->kmax, h->bmax, block), &gmax) != 0) {
-        dfree(tmp64);
-        return fail(h, SFM_ERR_ARG, "sfm_run: subdomain blocks too large for shared memory");
-    }
-    const int grid = std::min(gmax, std::max(p.nunits, 1));
+    int grid = 0;
+    rc = step_setup<P>(h, p.nunits, p, &grid);
+    if (rc != SFM_OK) { dfree(tmp64); return rc; }
     CK(h, cudaEventRecord(x->ev0, st));
-    cudaError_t e = sfm::launch_step<P>(p, block, grid, st);
+    cudaError_t e = sfm::launch_step<P>(p, grid, st);
     if (e != cudaSuccess) { dfree(tmp64); return cuda_fail(h, e, "step kernel launch"); }
     ++launches;
     CK(h, cudaEventRecord(x->ev1, st));
@@ -561,6 +608,61 @@ extern "C" int sfm_run(sfm_handle* h, int precision, double dt, int nsteps, cons
     if (precision == SFM_FP32X2)
         return run_impl<sfm::PolF32x2>(h, dt, nsteps, wavelet, traces, flags, kernel_ms);
     return fail(h, SFM_ERR_ARG, "sfm_run: unknown precision");
+}
+
+// Shape search for the stepping kernel: every candidate (consumer warps,
+// ring stages) that fits the shared memory runs a zero-source probe of
+// `nsteps` steps twice (the first run warms caches and the piece table),
+// timed by events around the step kernel alone; the fastest shape is kept
+// for `precision` on this handle.  The state stays zero, so no candidate
+// can go unstable, and the timing does not depend on the values.
+template <class P>
+static int autotune_impl(sfm_handle* h, int nsteps, int* ncw_out, int* nstage_out, double* us_out) {
+    static const int kNcw[] = {2, 4, 6, 8, 12, 16};
+    static const int kStage[] = {2, 3, 4, 6, 8};
+    sfm_ext* x = ext(h);
+    const int id = prec_id(P{});
+    const int ncw0 = x->ncw[id], nst0 = x->nstage[id];
+    std::vector<double> wav((size_t)h->nshots * nsteps, 0.0);
+    std::vector<double> tr((size_t)h->nshots * h->nrec * (nsteps + 1));
+    double best = 1e300;
+    int bn = ncw0, bs = nst0;
+    for (int nc : kNcw) {
+        for (int ns : kStage) {
+            int gmax = 0;
+            if (sfm::step_max_grid<P>(nc, sfm::step_smem_bytes<P>(h->kmax, h->bmax, ns), &gmax) != 0 ||
+                gmax < 1)
+                continue;
+            x->ncw[id] = nc;
+            x->nstage[id] = ns;
+            double ms = 0.0, ms2 = 0.0;
+            int rc = run_impl<P>(h, 1.0, nsteps, wav.data(), tr.data(), 0, &ms);
+            if (rc == SFM_OK) rc = run_impl<P>(h, 1.0, nsteps, wav.data(), tr.data(), 0, &ms2);
+            if (rc != SFM_OK) { x->ncw[id] = ncw0; x->nstage[id] = nst0; return rc; }
+            ms = std::min(ms, ms2);
+            if (ms < best) { best = ms; bn = nc; bs = ns; }
+        }
+    }
+    x->ncw[id] = bn;
+    x->nstage[id] = bs;
+    if (ncw_out) *ncw_out = bn;
+    if (nstage_out) *nstage_out = bs;
+    if (us_out) *us_out = best * 1e3 / nsteps;
+    return SFM_OK;
+}
+
+extern "C" int sfm_autotune(sfm_handle* h, int precision, int nsteps, int* ncw, int* nstage,
+                            double* us_per_step) {
+    if (!h) return fail(nullptr, SFM_ERR_ARG, "NULL handle");
+    if (!h->have_coef || !h->have_src || !h->have_rec)
+        return fail(h, SFM_ERR_STATE, "sfm_autotune: coefficients, sources and receivers must be set");
+    if (nsteps < 1) return fail(h, SFM_ERR_ARG, "sfm_autotune: nsteps < 1");
+    CK(h, cudaSetDevice(h->device));
+    if (precision == SFM_FP64) return autotune_impl<sfm::PolF64>(h, nsteps, ncw, nstage, us_per_step);
+    if (precision == SFM_FP32) return autotune_impl<sfm::PolF32>(h, nsteps, ncw, nstage, us_per_step);
+    if (precision == SFM_FP32X2)
+        return autotune_impl<sfm::PolF32x2>(h, nsteps, ncw, nstage, us_per_step);
+    return fail(h, SFM_ERR_ARG, "sfm_autotune: unknown precision");
 }
 
 // Largest eigenvalue of MM^{-1} KK.  One FP64 step of the stepping kernel
@@ -659,22 +761,18 @@ extern "C" int sfm_cfl_dt(sfm_handle* h, int iters, double* lambda_max, double* 
     p.dt2 = 1.0;
     p.bar = h->d_bar; p.err = h->d_err; p.timeout_ns = x->timeout_ns; p.skip_arrive = -1;
     p.Kx = Kx;
-    const int block = 256;
-    int gmax = 0;
-    if (sfm::step_max_grid<sfm::PolF64>(block,
-                                        sfm::step_smem_bytes<sfm::PolF64>(h->kmax, h->bmax, block),
-                                        &gmax) != 0) {
-        cleanup();
-        return fail(h, SFM_ERR_ARG, "sfm_cfl_dt: subdomain blocks too large for shared memory");
+    int grid = 0;
+    {
+        const int r2 = step_setup<sfm::PolF64>(h, h->nsub, p, &grid);
+        if (r2 != SFM_OK) { cleanup(); return r2; }
     }
-    const int grid = std::min(gmax, h->nsub);
     auto apply = [&](const double* in) -> cudaError_t {
         cudaError_t e;
         if ((e = cudaMemcpyAsync(U[0], in, n * sizeof(double), cudaMemcpyDeviceToDevice, st))) return e;
         if ((e = cudaMemsetAsync(dU, 0, n * sizeof(double), st))) return e;
         if ((e = cudaMemsetAsync(h->d_bar, 0, sizeof(unsigned int), st))) return e;
         if ((e = cudaMemsetAsync(h->d_err, 0, sizeof(int), st))) return e;
-        return sfm::launch_step<sfm::PolF64>(p, block, grid, st);
+        return sfm::launch_step<sfm::PolF64>(p, grid, st);
     };
     // q_1 = -MM^{-1} KK 1 (in dU), r_1 = MM q_1 = -KK 1 (in Kx)
     CKC(apply(X));

@@ -52,15 +52,20 @@ struct StepParams {
     int skip_arrive;             // test hook: this block skips its barrier arrival (-1: none)
     T* Kx;                       // optional: receives -KK U (the flux sums before the mass
                                  // blocks are applied), state layout; NULL when stepping
+    int ncw, nstage;             // consumer warps per block, shared-memory ring stages
+    const int* piece_ptr;        // [grid+1] pieces of each block
+    const int4* pieces;          // (unit, j0, j1, -): levels [j0, j1) of a unit
 };
 
 // launchers (step.cu); P is a number policy of numeric.cuh
 template <class P>
-cudaError_t launch_step(const StepParams<typename P::S>& p, int block, int grid, cudaStream_t st);
+cudaError_t launch_step(const StepParams<typename P::S>& p, int grid, cudaStream_t st);
 template <class P>
-int step_max_grid(int block, size_t smem, int* grid_out);
+int step_max_grid(int ncw, size_t smem, int* grid_out);
 template <class P>
-size_t step_smem_bytes(int kmax, int bmax, int block);
+size_t step_smem_bytes(int kmax, int bmax, int nstage);
+void build_pieces(int nunits, int nsub, const int* k_sub, int grid, std::vector<int>& ptr,
+                  std::vector<int4>& pieces);
 
 cudaError_t launch_face_H(const double* coef, const long long* gh1_off, const int* sub_b,
                           const int* face_off, const int* nbr, const long long* H_off,

@@ -128,8 +128,20 @@ extern "C" int sfm_run_static(int device, void* stream, int nsub, const int* k_s
         std::vector<int> fill(cnt.begin(), cnt.end() - 1);
         for (int i = 0; i < nrec_pairs; ++i) pairs[fill[rec_id[i]]++] = i;
     }
+    // ---- block shape, grid and per-block pieces (host) ----
+    const int ncw = 8, nstage = 6;
+    int gmax = 0;
+    if (sfm::step_max_grid<P>(ncw, sfm::step_smem_bytes<P>(kmax, bmax, nstage), &gmax) != 0)
+        return sfail(SFM_ERR_ARG, "sfm_run_static: subdomain blocks too large for shared memory");
+    long long levels = 0;
+    for (int u = 0; u < nshots * nsub; ++u) levels += k_sub[u % nsub];
+    const int grid = (int)std::max(1LL, std::min<long long>(gmax, levels));
+    std::vector<int> piece_ptr;
+    std::vector<int4> pieces;
+    sfm::build_pieces(nshots * nsub, nsub, k_sub, grid, piece_ptr, pieces);
     // ---- carve the scratch array ----
     Carve cv;
+    const size_t o_pp = cv.take<int>(piece_ptr.size()), o_pc = cv.take<int4>(pieces.size());
     const size_t o_b = cv.take<int>(nsub), o_k = cv.take<int>(nsub), o_fo = cv.take<int>(7 * (size_t)nsub),
                  o_nb = cv.take<int>(6 * (size_t)nsub), o_ho = cv.take<long long>(6 * (size_t)nsub),
                  o_to = cv.take<long long>(nsub), o_co = cv.take<long long>(nsub),
@@ -178,6 +190,8 @@ extern "C" int sfm_run_static(int device, void* stream, int nsub, const int* k_s
     SCK(put(o_ro, rp_off.data(), rp_off.size() * sizeof(long long)));
     SCK(put(o_rp, cnt.data(), cnt.size() * sizeof(int)));
     SCK(put(o_pr, pairs.data(), pairs.size() * sizeof(int)));
+    SCK(put(o_pp, piece_ptr.data(), piece_ptr.size() * sizeof(int)));
+    SCK(put(o_pc, pieces.data(), pieces.size() * sizeof(int4)));
     auto at = [&](size_t off) { return (void*)(base + off); };
     // every call shares the array: clear what has to start at zero
     for (auto u : o_U) SCK(cudaMemsetAsync(at(u), 0, (size_t)nshots * so * sizeof(double), st));
@@ -210,10 +224,9 @@ extern "C" int sfm_run_static(int device, void* stream, int nsub, const int* k_s
     p.dt2 = dt * dt;
     p.bar = (unsigned int*)at(o_bar); p.err = (int*)at(o_err);
     p.timeout_ns = 2000000000ull; p.skip_arrive = -1; p.Kx = nullptr;
-    int gmax = 0;
-    if (sfm::step_max_grid<P>(0, sfm::step_smem_bytes<P>(kmax, bmax, 0), &gmax) != 0)
-        return sfail(SFM_ERR_ARG, "sfm_run_static: subdomain blocks too large for shared memory");
-    SCK(sfm::launch_step<P>(p, 0, std::min(gmax, std::max(p.nunits, 1)), st));
+    p.ncw = ncw; p.nstage = nstage;
+    p.piece_ptr = (const int*)at(o_pp); p.pieces = (const int4*)at(o_pc);
+    SCK(sfm::launch_step<P>(p, grid, st));
     SCK(sfm::launch_reduce_traces<P>((const double*)at(o_part), (const int*)at(o_rp), (const int*)at(o_pr),
                                      nshots, nsteps, nrec, nrec_pairs, traces, (int*)at(o_bad), st));
     int herr = 0, bad = 0;

@@ -44,16 +44,15 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Block layout of the stepping kernel: NCW consumer warps do the arithmetic,
-// one producer warp streams the coefficient blocks into shared memory with
-// bulk asynchronous copies (the TMA engine) through a ring of NSTAGE stages.
-constexpr int NCW = 8;
-constexpr int NCT = NCW * 32;
-constexpr int STEP_BLOCK = NCT + 32;
-constexpr int NSTAGE = 6;
+// Block layout of the stepping kernel: p.ncw consumer warps do the
+// arithmetic, one producer warp streams the coefficient blocks into shared
+// memory with bulk asynchronous copies (the TMA engine) through a ring of
+// p.nstage stages.  Both are chosen at launch (see step_config).
+constexpr int NCW_MAX = 16;
+constexpr int STEP_BLOCK_MAX = (NCW_MAX + 1) * 32;
 
-__device__ __forceinline__ void cbar() {
-    asm volatile("bar.sync 1, %0;" ::"n"(NCT) : "memory");
+__device__ __forceinline__ void cbar(int nct) {
+    asm volatile("bar.sync 1, %0;" ::"r"(nct) : "memory");
 }
 
 __device__ __forceinline__ unsigned smem_u32(const void* ptr) {
@@ -114,9 +113,9 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 // Returns false (and sets *err) when it did not complete within timeout_ns
 // or another block reported an error; every block then leaves the kernel.
 __device__ bool grid_barrier(unsigned int* bar, unsigned int target, int* err,
-                             unsigned long long timeout_ns, int skip_arrive) {
+                             unsigned long long timeout_ns, int skip_arrive, int nct) {
     __shared__ int s_ok;
-    cbar();
+    cbar(nct);
     if (threadIdx.x == 0) {
         __threadfence();
         if ((int)blockIdx.x != skip_arrive) red_release_add_u32(bar, 1u);
@@ -133,7 +132,7 @@ __device__ bool grid_barrier(unsigned int* bar, unsigned int target, int* err,
         }
         s_ok = ok;
     }
-    cbar();
+    cbar(nct);
     return s_ok != 0;
 }
 
@@ -151,22 +150,6 @@ __device__ __forceinline__ T block_sum(T v, T* red) {
     return s;  // valid in thread 0
 }
 
-// Sum over the consumer threads in the policy's arithmetic (fixed order);
-// valid in thread 0.
-template <class P>
-__device__ __forceinline__ typename P::C block_sum_p(typename P::C v, typename P::C* red) {
-    for (int o = 16; o > 0; o >>= 1) v = P::add(v, P::shfl_xor(v, o));
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    cbar();
-    if (lane == 0) red[wid] = v;
-    cbar();
-    typename P::C s = P::zero();
-    if (threadIdx.x == 0) {
-        for (int w = 0; w < NCW; ++w) s = P::add(s, red[w]);
-    }
-    return s;
-}
-
 // Receiver readout of U (buffer `Ubuf`) at sample n.  Every (shot, pair)
 // item is one warp's compensated dot product of the pair's row with the
 // subdomain's state; items are spread over all consumer warps of the grid.
@@ -175,8 +158,8 @@ __device__ void readout(const StepParams<typename P::S>& p, const typename P::S*
     using C = typename P::C;
     const long long items = (long long)p.nshots * p.nrpairs;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (long long it = (long long)blockIdx.x * NCW + warp; it < items;
-         it += (long long)gridDim.x * NCW) {
+    for (long long it = (long long)blockIdx.x * p.ncw + warp; it < items;
+         it += (long long)gridDim.x * p.ncw) {
         const int q = (int)(it / p.nrpairs), r = (int)(it % p.nrpairs);
         const int s = p.rp_sub[r];
         const int kb = p.sub_k[s] * p.sub_b[s];
@@ -238,67 +221,75 @@ __device__ __forceinline__ void tile_row(const typename P::S* tiles, int nt, int
     if (q == 0) y[8 * I + r] = v;
 }
 
-// The coefficient blocks a block streams per (shot, subdomain) unit, in
-// order: Gamma_1..Gamma_k, then Gammahat_2..Gammahat_k.
-__device__ __forceinline__ long long unit_block_offset(long long T0, long long ltile, int m, int k) {
-    return (m < k) ? T0 + (long long)m * ltile : T0 + (long long)(m - k + 1) * ltile + ltile / 2;
+// Work of one block per time step: a list of pieces (unit, j0, j1), each a
+// contiguous range of levels of one (shot, subdomain) unit.  A piece streams
+// Gamma_j for j in [max(j0-1, 0), j1) (the extra level j0-1 gives phi_{j0-1},
+// needed by psi_{j0}) and then Gammahat_j for j in [max(j0, 1), j1); it
+// updates levels [max(j0, 1), j1) and, when j0 = 0, owns the unit's faces.
+__device__ __forceinline__ int piece_blocks(int j0, int j1) {
+    return (j1 - (j0 > 0 ? j0 - 1 : 0)) + (j1 - (j0 > 1 ? j0 : 1));
 }
 
 template <class P>
-__global__ void __launch_bounds__(STEP_BLOCK) step_kernel(StepParams<typename P::S> p) {
+__global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typename P::S> p) {
     using S = typename P::S;
     using C = typename P::C;
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int ncw = p.ncw, nct = ncw * 32, nstage = p.nstage;
     const int bpm = ((p.bmax + 7) / 8) * 8;
     const int stage_elems = (int)(sym_tiles(p.bmax) * 64);
     S* stages = reinterpret_cast<S*>(smem_raw);
-    C* sU = reinterpret_cast<C*>(stages + (size_t)NSTAGE * stage_elems);   // (kmax+1)*bpm
+    C* sU = reinterpret_cast<C*>(stages + (size_t)nstage * stage_elems);   // (kmax+1)*bpm
     C* sD = sU + (p.kmax + 1) * bpm;                     // kmax*bpm: Delta, then psi
     C* sPhi = sD + p.kmax * bpm;                         // kmax*bpm: phi, then a
-    C* red = sPhi + p.kmax * bpm;                        // 32
     unsigned long long* full = reinterpret_cast<unsigned long long*>(
-        (reinterpret_cast<uintptr_t>(red + 32) + 15) & ~(uintptr_t)15);
-    unsigned long long* empty = full + NSTAGE;
+        (reinterpret_cast<uintptr_t>(sPhi + p.kmax * bpm) + 15) & ~(uintptr_t)15);
+    unsigned long long* empty = full + nstage;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int pc0 = p.piece_ptr[blockIdx.x], pc1 = p.piece_ptr[blockIdx.x + 1];
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < NSTAGE; ++i) {
+        for (int i = 0; i < nstage; ++i) {
             mbar_init(full + i, 1);
-            mbar_init(empty + i, NCW);
+            mbar_init(empty + i, ncw);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
-    if (warp == NCW) {
+    if (warp == ncw) {
         // ------------------------------ producer ------------------------------
         if (lane != 0) return;
         long long g = 0;
         bool ok = true;
         for (int n = 0; n < p.nsteps && ok; ++n) {
-            for (int u = blockIdx.x; u < p.nunits && ok; u += gridDim.x) {
-                const int s = u % p.nsub;
-                const int b = p.sub_b[s], k = p.sub_k[s];
+            for (int pc = pc0; pc < pc1 && ok; ++pc) {
+                const int4 pe = p.pieces[pc];
+                const int s = pe.x % p.nsub, j0 = pe.y, j1 = pe.z;
+                const int b = p.sub_b[s];
                 const int nt = (b + 7) >> 3;
                 const long long ltile = 2LL * (nt * (nt + 1) / 2) * 64;
                 const unsigned bytes = (unsigned)((ltile / 2) * sizeof(S));
                 const long long T0 = p.coef_off[s];
-                for (int m = 0; m < 2 * k - 1; ++m, ++g) {
-                    const int st = (int)(g % NSTAGE);
-                    if (g >= NSTAGE &&
-                        !mbar_wait(empty + st, (unsigned)((g / NSTAGE - 1) & 1), p.err, p.timeout_ns)) {
+                const int jl = j0 > 0 ? j0 - 1 : 0, ja = j0 > 1 ? j0 : 1;
+                const int nblk = piece_blocks(j0, j1);
+                for (int m = 0; m < nblk; ++m, ++g) {
+                    const int st = (int)(g % nstage);
+                    if (g >= nstage &&
+                        !mbar_wait(empty + st, (unsigned)((g / nstage - 1) & 1), p.err, p.timeout_ns)) {
                         ok = false;
                         break;
                     }
+                    const long long off = (m < j1 - jl) ? T0 + (long long)(jl + m) * ltile
+                                                        : T0 + (long long)(ja + m - (j1 - jl)) * ltile + ltile / 2;
                     mbar_expect_tx(full + st, bytes);
-                    bulk_g2s(stages + (size_t)st * stage_elems,
-                             p.coef + unit_block_offset(T0, ltile, m, k), bytes, full + st);
+                    bulk_g2s(stages + (size_t)st * stage_elems, p.coef + off, bytes, full + st);
                 }
             }
         }
         // never leave with copies in flight: wait for every issued stage
-        for (long long h = (g > NSTAGE ? g - NSTAGE : 0); h < g; ++h)
-            mbar_wait(full + (int)(h % NSTAGE), (unsigned)((h / NSTAGE) & 1), p.err, p.timeout_ns);
+        for (long long h = (g > nstage ? g - nstage : 0); h < g; ++h)
+            mbar_wait(full + (int)(h % nstage), (unsigned)((h / nstage) & 1), p.err, p.timeout_ns);
         return;
     }
 
@@ -311,86 +302,93 @@ __global__ void __launch_bounds__(STEP_BLOCK) step_kernel(StepParams<typename P:
         S* mail = (n & 1) ? p.mail1 : p.mail0;
 
         // ---------------- phase A ----------------
-        for (int u = blockIdx.x; u < p.nunits; u += gridDim.x) {
+        for (int pc = pc0; pc < pc1; ++pc) {
+            const int4 pe = p.pieces[pc];
+            const int u = pe.x, j0 = pe.y, j1 = pe.z;
             const int q = u / p.nsub, s = u - q * p.nsub;
-            const int b = p.sub_b[s], k = p.sub_k[s], kb = k * b;
+            const int b = p.sub_b[s], k = p.sub_k[s];
             const int nt = (b + 7) >> 3, bp = nt * 8;
+            const int jl = j0 > 0 ? j0 - 1 : 0, ja = j0 > 1 ? j0 : 1, nl = j1 - jl;
             const long long so = q * p.state_stride + p.state_off[s];
             const S* Uc = Ucur + so;
             S* Un = Unxt + so;
             S* dU = p.dU + so;
             const long long sof = p.src_off[(long long)q * p.nsub + s];
             const C w = P::ld(p.wavelet + (long long)q * p.nsteps + n);
-            cbar();
-            // padded copies: level j occupies [j*bp, j*bp + b), zeros up to bp
-            for (int t = threadIdx.x; t < (k + 1) * bp; t += NCT) {
-                const int j = t / bp, i = t - j * bp;
+            cbar(nct);
+            // padded copies of levels jl..j1 (local index = level - jl)
+            for (int t = threadIdx.x; t < (nl + 1) * bp; t += nct) {
+                const int lj = t / bp, i = t - lj * bp, j = jl + lj;
                 sU[t] = (j < k && i < b) ? P::ld(Uc + j * b + i) : P::zero();
             }
-            cbar();
-            for (int t = threadIdx.x; t < k * bp; t += NCT) sD[t] = P::sub(sU[t + bp], sU[t]);
-            cbar();
-            // phi_j = Gamma_j Delta_j (blocks m = 0..k-1), then after psi,
-            // a_j = Gammahat_j psi_j (blocks m = k..2k-2, level j = m-k+1).
-            // Tile rows of the streamed blocks are handed to the warps round
-            // robin; each warp releases every block once it is done with it.
+            cbar(nct);
+            for (int t = threadIdx.x; t < nl * bp; t += nct) sD[t] = P::sub(sU[t + bp], sU[t]);
+            cbar(nct);
+            // phi_j = Gamma_j Delta_j for levels jl..j1-1, then after psi,
+            // a_j = Gammahat_j psi_j for levels ja..j1-1.  Tile rows of the
+            // streamed blocks go to the warps round robin; every warp waits
+            // for each block and releases it, so releases arrive in order.
             int task = 0;
             for (int half = 0; half < 2; ++half) {
-                const int m0 = half ? k : 0, m1 = half ? 2 * k - 1 : k;
-                for (int m = m0; m < m1; ++m, ++g) {
-                    const int st = (int)(g % NSTAGE);
-                    const int j = half ? m - k + 1 : m;
-                    const int first = (warp - task % NCW + NCW) % NCW;   // my first tile row
-                    // every warp waits for the block before releasing it, so that
-                    // releases of a stage arrive in block order
-                    if (!mbar_wait(full + st, (unsigned)((g / NSTAGE) & 1), p.err, p.timeout_ns))
+                const int lo = half ? ja : jl;
+                for (int j = lo; j < j1; ++j, ++g) {
+                    const int st = (int)(g % nstage);
+                    const int first = (warp - task % ncw + ncw) % ncw;
+                    if (!mbar_wait(full + st, (unsigned)((g / nstage) & 1), p.err, p.timeout_ns))
                         return;
-                    for (int I = first; I < nt; I += NCW)
-                        tile_row<P>(stages + (size_t)st * stage_elems, nt, I, sD + j * bp,
-                                    sPhi + j * bp);
+                    const int lj = j - jl;
+                    for (int I = first; I < nt; I += ncw)
+                        tile_row<P>(stages + (size_t)st * stage_elems, nt, I, sD + lj * bp,
+                                    sPhi + lj * bp);
                     __syncwarp();
                     if (lane == 0) mbar_arrive(empty + st);
                     task += nt;
                 }
-                cbar();
+                cbar(nct);
                 if (half == 0) {
-                    // (2.1) publish face data; psi_j for the interior levels
-                    S* my_mail = mail + q * p.mail_stride + p.mail_off[s];
-                    for (int t = threadIdx.x; t < kb; t += NCT) {
-                        const int j = t / b, i = t - j * b;
-                        const C srcv = (sof >= 0) ? P::mul(P::ld(p.src + sof + t), w) : P::zero();
-                        if (j == 0) P::st(my_mail + i, P::add(sPhi[i], srcv));
-                        else sD[j * bp + i] = P::add(P::sub(sPhi[j * bp + i], sPhi[(j - 1) * bp + i]), srcv);
+                    // (2.1) publish face data; psi_j for the updated levels
+                    if (j0 == 0) {
+                        S* my_mail = mail + q * p.mail_stride + p.mail_off[s];
+                        for (int i = threadIdx.x; i < b; i += nct) {
+                            const C srcv = (sof >= 0) ? P::mul(P::ld(p.src + sof + i), w) : P::zero();
+                            P::st(my_mail + i, P::add(sPhi[i], srcv));
+                        }
                     }
-                    cbar();
+                    for (int t = threadIdx.x; t < (j1 - ja) * b; t += nct) {
+                        const int j = ja + t / b, i = t % b, lj = j - jl;
+                        const C srcv = (sof >= 0) ? P::mul(P::ld(p.src + sof + j * b + i), w) : P::zero();
+                        sD[lj * bp + i] = P::add(P::sub(sPhi[lj * bp + i], sPhi[(lj - 1) * bp + i]), srcv);
+                    }
+                    cbar(nct);
                 }
             }
-            // (2.2) interior update, Eq. (19)
-            if (p.Kx)
-                for (int t = b + threadIdx.x; t < kb; t += NCT)
-                    P::st(p.Kx + so + t, sD[(t / b) * bp + (t % b)]);
-            for (int t = b + threadIdx.x; t < kb; t += NCT) {
-                const int j = t / b, i = t - j * b;
-                const C d = P::add(P::ld(dU + t), P::mul(dt2, sPhi[j * bp + i]));
-                P::st(dU + t, d);
-                P::st(Un + t, P::add(sU[j * bp + i], d));
+            // (2.2) interior update of levels ja..j1-1, Eq. (19)
+            for (int t = threadIdx.x; t < (j1 - ja) * b; t += nct) {
+                const int j = ja + t / b, i = t % b, lj = j - jl;
+                if (p.Kx) P::st(p.Kx + so + j * b + i, sD[lj * bp + i]);
+                const C d = P::add(P::ld(dU + j * b + i), P::mul(dt2, sPhi[lj * bp + i]));
+                P::st(dU + j * b + i, d);
+                P::st(Un + j * b + i, P::add(sU[lj * bp + i], d));
             }
         }
 
         if (!grid_barrier(p.bar, (unsigned)(n + 1) * gridDim.x, p.err, p.timeout_ns,
-                          p.skip_arrive))
+                          p.skip_arrive, nct))
             return;
 
         // ---------------- phase B: faces, Eq. (18) ----------------
-        for (int u = blockIdx.x; u < p.nunits; u += gridDim.x) {
+        for (int pc = pc0; pc < pc1; ++pc) {
+            const int4 pe = p.pieces[pc];
+            if (pe.y != 0) continue;                     // faces belong to the level-0 piece
+            const int u = pe.x;
             const int q = u / p.nsub, s = u - q * p.nsub;
             const int b = p.sub_b[s];
             const long long so = q * p.state_stride + p.state_off[s];
             const S* mine = mail + q * p.mail_stride + p.mail_off[s];
             const int* fo = p.face_off + s * 7;
-            cbar();
+            cbar(nct);
             // sum of both sides' face data, lower subdomain index first
-            for (int t = threadIdx.x; t < b; t += NCT) {
+            for (int t = threadIdx.x; t < b; t += nct) {
                 int f = 0;
                 while (t >= fo[f + 1]) ++f;
                 const int nb = p.nbr[s * 6 + f];
@@ -403,8 +401,8 @@ __global__ void __launch_bounds__(STEP_BLOCK) step_kernel(StepParams<typename P:
                 sD[t] = v;
                 if (p.Kx) P::st(p.Kx + so + t, v);
             }
-            cbar();
-            for (int t = threadIdx.x; t < b; t += NCT) {
+            cbar(nct);
+            for (int t = threadIdx.x; t < b; t += nct) {
                 int f = 0;
                 while (t >= fo[f + 1]) ++f;
                 const int m = fo[f + 1] - fo[f], i = t - fo[f];
@@ -422,49 +420,76 @@ __global__ void __launch_bounds__(STEP_BLOCK) step_kernel(StepParams<typename P:
     }
     // final readout of U^{nsteps}, after every face update of the last step
     if (!grid_barrier(p.bar, (unsigned)(p.nsteps + 1) * gridDim.x, p.err, p.timeout_ns,
-                      p.skip_arrive))
+                      p.skip_arrive, nct))
         return;
     readout<P>(p, p.U[p.nsteps % 3], p.nsteps);
 }
 
 template <class P>
-size_t step_smem_bytes(int kmax, int bmax, int block) {
-    (void)block;
+size_t step_smem_bytes(int kmax, int bmax, int nstage) {
     const size_t bp = (size_t)((bmax + 7) / 8) * 8;
-    size_t bytes = (size_t)NSTAGE * sym_tiles(bmax) * 64 * sizeof(typename P::S);
-    bytes += sizeof(typename P::C) * ((size_t)(kmax + 1) * bp + 2 * (size_t)kmax * bp + 32);
+    size_t bytes = (size_t)nstage * sym_tiles(bmax) * 64 * sizeof(typename P::S);
+    bytes += sizeof(typename P::C) * ((size_t)(kmax + 1) * bp + 2 * (size_t)kmax * bp);
     bytes = (bytes + 15) & ~(size_t)15;
-    return bytes + 2 * NSTAGE * sizeof(unsigned long long);
+    return bytes + 2 * nstage * sizeof(unsigned long long);
 }
 
 template <class P>
-int step_max_grid(int block, size_t smem, int* grid_out) {
-    (void)block;
+int step_max_grid(int ncw, size_t smem, int* grid_out) {
     int per_sm = 0, nsm = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(step_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<P>, STEP_BLOCK, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<P>, (ncw + 1) * 32, smem);
     if (per_sm < 1) return -1;
     *grid_out = per_sm * nsm;
     return 0;
 }
 
 template <class P>
-cudaError_t launch_step(const StepParams<typename P::S>& p, int block, int grid, cudaStream_t st) {
-    (void)block;
-    const size_t smem = step_smem_bytes<P>(p.kmax, p.bmax, STEP_BLOCK);
+cudaError_t launch_step(const StepParams<typename P::S>& p, int grid, cudaStream_t st) {
+    const size_t smem = step_smem_bytes<P>(p.kmax, p.bmax, p.nstage);
     cudaError_t e = cudaFuncSetAttribute(step_kernel<P>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     StepParams<typename P::S> pc = p;
     void* args[] = {&pc};
-    return cudaLaunchCooperativeKernel((void*)step_kernel<P>, dim3(grid), dim3(STEP_BLOCK), args,
-                                       smem, st);
+    return cudaLaunchCooperativeKernel((void*)step_kernel<P>, dim3(grid), dim3((p.ncw + 1) * 32),
+                                       args, smem, st);
+}
+
+// Pieces of work per block: the (unit, level) sequence, unit-major, cut into
+// `grid` contiguous ranges of (nearly) equal length.  A unit is never cut at
+// level 1: a piece starting there would read the level-0 face blocks, which
+// the level-0 piece updates after the device-wide barrier, with no barrier
+// before the next step's phase A; pieces starting at level >= 2 read only
+// interior levels, which are written before the barrier.
+void build_pieces(int nunits, int nsub, const int* k_sub, int grid, std::vector<int>& ptr,
+                  std::vector<int4>& pieces) {
+    long long total = 0;
+    for (int u = 0; u < nunits; ++u) total += k_sub[u % nsub];
+    ptr.assign(grid + 1, 0);
+    pieces.clear();
+    int u = 0, j = 0;
+    long long pos = 0;
+    for (int c = 0; c < grid; ++c) {
+        const long long end = total * (c + 1) / grid;
+        ptr[c] = (int)pieces.size();
+        while (pos < end && u < nunits) {
+            const int k = k_sub[u % nsub];
+            int take = (int)std::min<long long>(end - pos, k - j);
+            if (j + take == 1 && k > 1) take = 2 - j;   // no cut at level 1
+            pieces.push_back(make_int4(u, j, j + take, 0));
+            j += take;
+            pos += take;
+            if (j == k) { ++u; j = 0; }
+        }
+    }
+    ptr[grid] = (int)pieces.size();
 }
 
 #define SFM_INST(P)                                                                             \
-    template cudaError_t launch_step<P>(const StepParams<P::S>&, int, int, cudaStream_t);       \
+    template cudaError_t launch_step<P>(const StepParams<P::S>&, int, cudaStream_t);            \
     template int step_max_grid<P>(int, size_t, int*);                                           \
     template size_t step_smem_bytes<P>(int, int, int);
 SFM_INST(PolF64)

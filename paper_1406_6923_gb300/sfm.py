@@ -34,7 +34,8 @@ SFM_DEVICE_PTR = 1
 EXPORTS = ["sfm_create", "sfm_destroy", "sfm_last_error", "sfm_set_stream", "sfm_set_topology",
            "sfm_set_coeffs", "sfm_get_coeffs", "sfm_set_sources", "sfm_set_receivers",
            "sfm_run", "sfm_cfl_dt", "sfm_last_launches", "sfm_debug_set", "sfm_set_model",
-           "sfm_build_roms", "sfm_project_sources", "sfm_project_receivers", "sfm_free_build", "sfm_run_static"]
+           "sfm_build_roms", "sfm_project_sources", "sfm_project_receivers", "sfm_free_build", "sfm_run_static",
+           "sfm_autotune"]
 
 
 class sfm_build_report(C.Structure):
@@ -87,6 +88,7 @@ def load(path=LIB_PATH):
         "sfm_free_build": (_i, [_p]),
         "sfm_run_static": (_i, [_i, _p, _i, _ip, _ip, _ip, _p, _i, _i, _ip, _ip, _p, _i, _i, _ip,
                                 _ip, _p, C.c_double, _i, _p, _p]),
+        "sfm_autotune": (_i, [_p, _i, _i, _ip, _ip, _dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -189,6 +191,16 @@ def sfm_cfl_dt(h, iters=300):
     dt = C.c_double(0.0)
     _check(h, load().sfm_cfl_dt(h, int(iters), C.byref(lam), C.byref(dt)))
     return lam.value, dt.value
+
+
+def sfm_autotune(h, precision, nsteps=200):
+    """Returns (consumer warps, ring stages, microseconds per time step)."""
+    ncw = C.c_int(0)
+    nst = C.c_int(0)
+    us = C.c_double(0.0)
+    _check(h, load().sfm_autotune(h, int(precision), int(nsteps), C.byref(ncw), C.byref(nst),
+                                  C.byref(us)))
+    return ncw.value, nst.value, us.value
 
 
 def sfm_last_launches(h):

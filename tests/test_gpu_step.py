@@ -113,6 +113,30 @@ def test_device_pointer_path_matches_host_path(sfm, uneven):
         sfm.sfm_destroy(h)
 
 
+@pytest.mark.parametrize("precision", [0, 2])
+def test_block_shapes_give_identical_traces(sfm, uneven, precision):
+    """Consumer warps and ring stages change the grid, the per-block pieces
+    (units cut at different levels) and which warp runs a tile row, never the
+    order of any sum: traces are bitwise equal across shapes, and the shape
+    the autotuner picks is one of its candidates."""
+    p, rs, dt, n, w, ref = uneven
+    h = sfm.sfm_create(0)
+    try:
+        load_into(sfm, h, rs)
+        base, _ = sfm.sfm_run(h, precision, dt, n, w, rs.nshots, rs.nrec)
+        for ncw, nst in ((1, 2), (2, 3), (6, 4), (16, 8), (3, 16)):
+            sfm.sfm_debug_set(h, 3, ncw)
+            sfm.sfm_debug_set(h, 4, nst)
+            got, _ = sfm.sfm_run(h, precision, dt, n, w, rs.nshots, rs.nrec)
+            assert np.array_equal(got, base), (ncw, nst)
+        ncw, nst, us = sfm.sfm_autotune(h, precision, 50)
+        assert ncw in (2, 4, 6, 8, 12, 16) and nst in (2, 3, 4, 6, 8) and us > 0
+        got, _ = sfm.sfm_run(h, precision, dt, n, w, rs.nshots, rs.nrec)
+        assert np.array_equal(got, base)
+    finally:
+        sfm.sfm_destroy(h)
+
+
 def test_coefficients_round_trip(sfm, uneven):
     p, rs, dt, n, w, ref = uneven
     h = sfm.sfm_create(0)
