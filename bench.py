@@ -50,9 +50,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sfm", choices=["sfm", "reference"])
     ap.add_argument("--nsteps", type=int, default=None, help="time steps per run (default: 4000)")
-    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "fp32x2", "fp64"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32f", "fp32", "fp32x2", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=60)
+    ap.add_argument("--shape", default=None,
+                    help="fixed stepping block shape 'warps,stages' instead of the autotuner's")
     return ap.parse_args()
 
 
@@ -242,6 +244,10 @@ def main():
     dt = p.dt_safety * dtc
     dtf = fine_dt(p)
     nshots, nrec = p.nshots, p.nrec
+    if args.shape:
+        fixed = [int(v) for v in args.shape.split(",")]
+        sfm.sfm_debug_set(h, 3, fixed[0])
+        sfm.sfm_debug_set(h, 4, fixed[1])
     wav = torch.tensor(inputs.wavelet_samples(p, dt, nsteps), dtype=torch.float64, device="cuda")
     tr = torch.empty((nshots, nrec, nsteps + 1), dtype=torch.float64, device="cuda")
 
@@ -254,9 +260,10 @@ def main():
     run(sfm.SFM_FP64)
     torch.cuda.synchronize()
     ref = tr.cpu().numpy()
-    modes = {"fp32": sfm.SFM_FP32, "fp32x2": sfm.SFM_FP32X2, "fp64": sfm.SFM_FP64}
+    modes = {"fp32f": sfm.SFM_FP32F, "fp32": sfm.SFM_FP32, "fp32x2": sfm.SFM_FP32X2,
+             "fp64": sfm.SFM_FP64}
     errors = {"fp64": 0.0}
-    for name in ("fp32", "fp32x2"):
+    for name in ("fp32f", "fp32", "fp32x2"):
         try:
             run(modes[name])
             torch.cuda.synchronize()
@@ -264,14 +271,17 @@ def main():
         except sfm.SfmError as e:
             errors[name] = float("inf") if e.code == sfm.SFM_ERR_UNSTABLE else None
     if args.precision == "auto":
-        chosen = next(n for n in ("fp32", "fp32x2", "fp64")
+        chosen = next(n for n in ("fp32f", "fp32", "fp32x2", "fp64")
                       if errors.get(n) is not None and errors[n] <= GATE)
     else:
         chosen = args.precision
     prec = modes[chosen]
     # block shape of the stepping kernel, picked by the library's autotuner
     # (zero-source probes, outside the timed region)
-    tune_ncw, tune_nst, tune_us = sfm.sfm_autotune(h, prec, 200)
+    if args.shape:
+        tune_ncw, tune_nst, tune_us = fixed[0], fixed[1], None
+    else:
+        tune_ncw, tune_nst, tune_us = sfm.sfm_autotune(h, prec, 200)
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
     for _ in range(args.warmup):
@@ -317,7 +327,7 @@ def main():
 
     # roofline of the persistent stepping kernel
     pk, pk_kind = peaks()
-    word = {"fp32": 4, "fp32x2": 8, "fp64": 8}[chosen]
+    word = {"fp32f": 4, "fp32": 4, "fp32x2": 8, "fp64": 8}[chosen]
     bytes_step = algorithmic_bytes_per_step(p.nsub, 48, 16, 8, count_rpairs(sfm, h, p), word)
     kms = statistics.mean(kern_ms)
     achieved = bytes_step * nsteps / (kms * 1e-3) / 1e9
@@ -338,7 +348,7 @@ def main():
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": {"fp32": "f32", "fp32x2": "f32x2", "fp64": "f64"}[chosen],
+           "vs_baseline": None, "dtype": {"fp32f": "f32", "fp32": "f32", "fp32x2": "f32x2", "fp64": "f64"}[chosen],
            "data": "synthetic",
            "config": {"workload": p.name, "cells": ncell, "subdomains": p.nsub, "b": 48, "k": 16,
                       "shots": nshots, "receivers": nrec, "time_steps": nsteps,

@@ -53,8 +53,13 @@ enum sfm_status {
 enum sfm_precision {
     SFM_FP64 = 0,            /* FP64 coefficients, state and sums              */
     SFM_FP32 = 1,            /* FP32 coefficients, state and sums              */
-    SFM_FP32X2 = 2           /* two-float numbers (hi + lo FP32, ~48-bit
+    SFM_FP32X2 = 2,          /* two-float numbers (hi + lo FP32, ~48-bit
                                 significand) with compensated FP32 arithmetic */
+    SFM_FP32F = 3            /* FP32 state and sums; each S-fraction block
+                                applied through its FP32 Cholesky factor,
+                                Gamma = L L^T (factored in FP64 on the GPU),
+                                which keeps it positive semi-definite under
+                                rounding                                       */
 };
 
 /* flags for sfm_run */
@@ -132,7 +137,9 @@ int sfm_set_receivers(sfm_handle* h, int nrec, int npairs, const int* pair_rec,
  * n = 0..nsteps-1 the right-hand sides of Eqs. 18-19 (with the source term
  * f_q(t_n)) are evaluated at t_n = n*dt and
  *     delta^{n+1} = delta^n + dt^2 a^n,  U^{n+1} = U^n + delta^{n+1}.
- *   precision      SFM_FP64, SFM_FP32 or SFM_FP32X2 (coefficients, state, sums)
+ *   precision      SFM_FP64, SFM_FP32, SFM_FP32X2 or SFM_FP32F (coefficients,
+ *                  state, sums); SFM_FP32F first factors every block used
+ *                  (SFM_ERR_NOT_SPD if one is not positive definite in FP64)
  *   wavelet        [nshots][nsteps] FP64 samples f_q(t_n)
  *   traces         [nshots][nrec][nsteps+1] FP64 output, d_r(t_n), n=0..nsteps
  *   flags          SFM_DEVICE_PTR: wavelet and traces are device pointers
@@ -143,7 +150,7 @@ int sfm_set_receivers(sfm_handle* h, int nrec, int npairs, const int* pair_rec,
  * device-wide barrier between the face-data publication (step 2.1, with
  * 2.2) and the face update (step 2.3).
  * Errors: SFM_ERR_STATE (missing data), SFM_ERR_TIMEOUT (barrier timed out),
- * SFM_ERR_UNSTABLE (non-finite traces), SFM_ERR_CUDA.
+ * SFM_ERR_UNSTABLE (non-finite traces), SFM_ERR_NOT_SPD, SFM_ERR_CUDA.
  */
 int sfm_run(sfm_handle* h, int precision, double dt, int nsteps, const double* wavelet,
             double* traces, int flags, double* kernel_ms);
@@ -161,7 +168,8 @@ int sfm_cfl_dt(sfm_handle* h, int iters, double* lambda_max, double* dt_cfl);
  * Shape search for the stepping kernel of `precision` on this handle (no
  * counterpart in the paper, whose method fixes no launch shape).  Each
  * candidate block shape - consumer warps in {2,4,6,8,12,16} times
- * coefficient ring stages in {2,3,4,6,8}, those whose shared memory fits -
+ * coefficient ring stages in {2,3,4,6,8,12,16}, those whose shared memory
+ * fits (for SFM_FP32F only stage counts that are multiples of the warps) -
  * steps the coupled system `nsteps` steps from a zero source twice; the
  * fastest (step kernel alone, CUDA events) becomes the shape of later
  * sfm_run calls in that precision.  Results do not depend on the shape:
@@ -285,7 +293,8 @@ int sfm_last_launches(const sfm_handle* h, int* launches);
  *          SFM_ERR_TIMEOUT with the context still usable;
  *   key 3: consumer warps per stepping block (1..16), all precisions;
  *   key 4: coefficient ring stages per stepping block (2..16), all
- *          precisions (keys 3 and 4 override sfm_autotune's choice).
+ *          precisions (keys 3 and 4 override sfm_autotune's choice; for
+ *          SFM_FP32F the stages are rounded up to a multiple of the warps).
  * Errors: SFM_ERR_ARG for an unknown key or a value out of range.
  */
 int sfm_debug_set(sfm_handle* h, int key, long long value);

@@ -2,6 +2,11 @@
 //
 //   PolF64   : FP64 storage and arithmetic.
 //   PolF32   : FP32 storage and arithmetic.
+//   PolF32F  : FP32 storage and arithmetic with every S-fraction block held
+//              as its Cholesky factor (Gamma = L L^T), applied as L (L^T x):
+//              the factored form stays positive semi-definite whatever the
+//              rounding of L, where FP32-rounded deep-ROM blocks (condition
+//              numbers up to ~1e14) turn indefinite and the leapfrog diverges.
 //   PolF32x2 : "two-float" numbers x = hi + lo (two FP32 words, ~48-bit
 //              significand) with FP32 arithmetic made exact by error-free
 //              transformations: Knuth's two-sum, the FMA two-product
@@ -45,6 +50,7 @@ __device__ __forceinline__ df df_mul(df x, df y) {
 }
 
 struct PolF64 {
+    static constexpr bool factored = false;
     using S = double;   // storage
     using C = double;   // value in registers / shared memory
     static constexpr int kind = 0;
@@ -75,6 +81,7 @@ struct PolF64 {
 };
 
 struct PolF32 {
+    static constexpr bool factored = false;
     using S = float;
     using C = float;
     static constexpr int kind = 1;
@@ -104,6 +111,7 @@ struct PolF32 {
 };
 
 struct PolF32x2 {
+    static constexpr bool factored = false;
     using S = float2;
     using C = df;
     static constexpr int kind = 2;
@@ -164,6 +172,11 @@ struct PolF32x2 {
         const df t = two_sum(a.s, a.e);
         return t;
     }
+};
+
+struct PolF32F : PolF32 {
+    static constexpr bool factored = true;
+    static constexpr int kind = 3;
 };
 
 }  // namespace sfm

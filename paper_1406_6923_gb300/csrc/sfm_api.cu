@@ -85,6 +85,7 @@ struct sfm_ext {
     Cache<float> c32;
     Cache<double> c64;
     Cache<float2> c2;
+    Cache<float> c32f;                 // factored FP32 coefficients
     RunBufs<float> r32;
     RunBufs<double> r64;
     RunBufs<float2> r2;
@@ -93,9 +94,9 @@ struct sfm_ext {
     int* d_bad = nullptr;
     unsigned long long timeout_ns = 2000000000ull;
     int skip_arrive = -1;
-    // stepping block shape per precision (FP64, FP32, FP32x2): consumer
+    // stepping block shape per precision (FP64, FP32, FP32x2, FP32F): consumer
     // warps and coefficient ring stages; sfm_autotune overwrites these
-    int ncw[3] = {8, 8, 8}, nstage[3] = {4, 4, 4};
+    int ncw[4] = {8, 8, 8, 8}, nstage[4] = {4, 4, 4, 4};
     int* d_piece_ptr = nullptr;
     int4* d_pieces = nullptr;
     int piece_grid = -1, piece_units = -1;
@@ -108,6 +109,7 @@ static void invalidate(sfm_handle* h) {
     ext(h)->c32.release();
     ext(h)->c64.release();
     ext(h)->c2.release();
+    ext(h)->c32f.release();
 }
 
 extern "C" {
@@ -147,7 +149,7 @@ int sfm_destroy(sfm_handle* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     sfm_ext* x = ext(h);
     if (x) {
-        x->c32.release(); x->c64.release(); x->c2.release();
+        x->c32.release(); x->c64.release(); x->c2.release(); x->c32f.release();
         x->r32.release(); x->r64.release(); x->r2.release();
         dfree(x->d_traces); dfree(x->d_bad); dfree(x->d_piece_ptr); dfree(x->d_pieces);
         if (x->ev0) cudaEventDestroy(x->ev0);
@@ -398,12 +400,12 @@ int sfm_debug_set(sfm_handle* h, int key, long long value) {
     if (key == 2) { ext(h)->skip_arrive = (int)value; return SFM_OK; }
     if (key == 3) {
         if (value < 1 || value > 16) return fail(h, SFM_ERR_ARG, "sfm_debug_set: consumer warps 1..16");
-        for (int i = 0; i < 3; ++i) ext(h)->ncw[i] = (int)value;
+        for (int i = 0; i < 4; ++i) ext(h)->ncw[i] = (int)value;
         return SFM_OK;
     }
     if (key == 4) {
         if (value < 2 || value > 16) return fail(h, SFM_ERR_ARG, "sfm_debug_set: ring stages 2..16");
-        for (int i = 0; i < 3; ++i) ext(h)->nstage[i] = (int)value;
+        for (int i = 0; i < 4; ++i) ext(h)->nstage[i] = (int)value;
         return SFM_OK;
     }
     return fail(h, SFM_ERR_ARG, "sfm_debug_set: unknown key");
@@ -419,14 +421,10 @@ int sfm_last_launches(const sfm_handle* h, int* launches) {
 
 // ---------------------------------------------------------------------------
 
-template <typename T>
-static Cache<T>& cache_of(sfm_handle* h);
-template <>
-Cache<float>& cache_of<float>(sfm_handle* h) { return ext(h)->c32; }
-template <>
-Cache<double>& cache_of<double>(sfm_handle* h) { return ext(h)->c64; }
-template <>
-Cache<float2>& cache_of<float2>(sfm_handle* h) { return ext(h)->c2; }
+static Cache<double>& cache_of(sfm_handle* h, sfm::PolF64) { return ext(h)->c64; }
+static Cache<float>& cache_of(sfm_handle* h, sfm::PolF32) { return ext(h)->c32; }
+static Cache<float2>& cache_of(sfm_handle* h, sfm::PolF32x2) { return ext(h)->c2; }
+static Cache<float>& cache_of(sfm_handle* h, sfm::PolF32F) { return ext(h)->c32f; }
 template <typename T>
 static RunBufs<T>& bufs_of(sfm_handle* h);
 template <>
@@ -439,7 +437,7 @@ RunBufs<float2>& bufs_of<float2>(sfm_handle* h) { return ext(h)->r2; }
 template <class P>
 static int prepare(sfm_handle* h) {
     using T = typename P::S;
-    Cache<T>& c = cache_of<T>(h);
+    auto& c = cache_of(h, P{});
     if (c.valid) return SFM_OK;
     c.release();
     cudaStream_t st = h->stream;
@@ -447,12 +445,24 @@ static int prepare(sfm_handle* h) {
     CK(h, dalloc(c.H, (size_t)h->nH));
     CK(h, dalloc(c.src, (size_t)h->nsrc));
     CK(h, dalloc(c.rrows, (size_t)h->nrrow));
-    CK(h, sfm::launch_pack_tiles<P>(h->d_coef64, h->d_coef_off, h->d_tcoef_off, h->d_b, h->d_k,
-                                    h->nsub, c.coef, st));
+    int bad = 0;
+    if constexpr (P::factored) {
+        CK(h, cudaMemsetAsync(ext(h)->d_bad, 0, sizeof(int), st));
+        CK(h, sfm::launch_factor_tiles(h->d_coef64, h->d_coef_off, h->d_tcoef_off, h->d_b, h->d_k,
+                                       h->nsub, h->kmax, c.coef, ext(h)->d_bad, st));
+        CK(h, cudaMemcpyAsync(&bad, ext(h)->d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    } else {
+        CK(h, sfm::launch_pack_tiles<P>(h->d_coef64, h->d_coef_off, h->d_tcoef_off, h->d_b, h->d_k,
+                                        h->nsub, c.coef, st));
+    }
     CK(h, sfm::launch_convert<P>(h->d_H64, c.H, (size_t)h->nH, st));
     CK(h, sfm::launch_convert<P>(h->d_src64, c.src, (size_t)h->nsrc, st));
     CK(h, sfm::launch_convert<P>(h->d_rrows64, c.rrows, (size_t)h->nrrow, st));
     CK(h, cudaStreamSynchronize(st));
+    if (bad) {
+        c.release();
+        return fail(h, SFM_ERR_NOT_SPD, "factored FP32: an S-fraction block is not positive definite");
+    }
     c.valid = true;
     return SFM_OK;
 }
@@ -460,6 +470,7 @@ static int prepare(sfm_handle* h) {
 static int prec_id(sfm::PolF64) { return SFM_FP64; }
 static int prec_id(sfm::PolF32) { return SFM_FP32; }
 static int prec_id(sfm::PolF32x2) { return SFM_FP32X2; }
+static int prec_id(sfm::PolF32F) { return SFM_FP32F; }
 
 // Grid of the persistent stepping kernel (co-resident blocks for the
 // chosen shape, at most one per level of work) and the per-block pieces.
@@ -467,9 +478,13 @@ template <class P>
 static int step_setup(sfm_handle* h, int nunits, sfm::StepParams<typename P::S>& p, int* grid_out) {
     sfm_ext* x = ext(h);
     const int id = prec_id(P{});
+    const int ncw = x->ncw[id];
+    int nstage = x->nstage[id];
+    // factored blocks are owned by warp (block index mod ncw) through fixed
+    // stages: the ring depth must be a multiple of the warp count
+    if (P::factored) nstage = (nstage + ncw - 1) / ncw * ncw;
     int gmax = 0;
-    if (sfm::step_max_grid<P>(x->ncw[id], sfm::step_smem_bytes<P>(h->kmax, h->bmax, x->nstage[id]),
-                              &gmax) != 0)
+    if (sfm::step_max_grid<P>(ncw, sfm::step_smem_bytes<P>(h->kmax, h->bmax, nstage), &gmax) != 0)
         return fail(h, SFM_ERR_ARG, "stepping: subdomain blocks too large for shared memory");
     long long levels = 0;
     for (int u = 0; u < nunits; ++u) levels += h->k[u % h->nsub];
@@ -483,8 +498,8 @@ static int step_setup(sfm_handle* h, int nunits, sfm::StepParams<typename P::S>&
         x->piece_grid = grid;
         x->piece_units = nunits;
     }
-    p.ncw = x->ncw[id];
-    p.nstage = x->nstage[id];
+    p.ncw = ncw;
+    p.nstage = nstage;
     p.piece_ptr = x->d_piece_ptr;
     p.pieces = x->d_pieces;
     *grid_out = grid;
@@ -506,7 +521,7 @@ static int run_impl(sfm_handle* h, double dt, int nsteps, const double* wavelet,
     sfm_ext* x = ext(h);
     int rc = prepare<P>(h);
     if (rc != SFM_OK) return rc;
-    Cache<T>& c = cache_of<T>(h);
+    auto& c = cache_of(h, P{});
     RunBufs<T>& r = bufs_of<T>(h);
     cudaStream_t st = h->stream;
     const size_t nst = (size_t)h->nshots * h->nstate;
@@ -607,6 +622,8 @@ extern "C" int sfm_run(sfm_handle* h, int precision, double dt, int nsteps, cons
         return run_impl<sfm::PolF32>(h, dt, nsteps, wavelet, traces, flags, kernel_ms);
     if (precision == SFM_FP32X2)
         return run_impl<sfm::PolF32x2>(h, dt, nsteps, wavelet, traces, flags, kernel_ms);
+    if (precision == SFM_FP32F)
+        return run_impl<sfm::PolF32F>(h, dt, nsteps, wavelet, traces, flags, kernel_ms);
     return fail(h, SFM_ERR_ARG, "sfm_run: unknown precision");
 }
 
@@ -619,7 +636,7 @@ extern "C" int sfm_run(sfm_handle* h, int precision, double dt, int nsteps, cons
 template <class P>
 static int autotune_impl(sfm_handle* h, int nsteps, int* ncw_out, int* nstage_out, double* us_out) {
     static const int kNcw[] = {2, 4, 6, 8, 12, 16};
-    static const int kStage[] = {2, 3, 4, 6, 8};
+    static const int kStage[] = {2, 3, 4, 6, 8, 12, 16};
     sfm_ext* x = ext(h);
     const int id = prec_id(P{});
     const int ncw0 = x->ncw[id], nst0 = x->nstage[id];
@@ -629,6 +646,7 @@ static int autotune_impl(sfm_handle* h, int nsteps, int* ncw_out, int* nstage_ou
     int bn = ncw0, bs = nst0;
     for (int nc : kNcw) {
         for (int ns : kStage) {
+            if (P::factored && ns % nc != 0) continue;   // see step_setup
             int gmax = 0;
             if (sfm::step_max_grid<P>(nc, sfm::step_smem_bytes<P>(h->kmax, h->bmax, ns), &gmax) != 0 ||
                 gmax < 1)
@@ -662,6 +680,8 @@ extern "C" int sfm_autotune(sfm_handle* h, int precision, int nsteps, int* ncw, 
     if (precision == SFM_FP32) return autotune_impl<sfm::PolF32>(h, nsteps, ncw, nstage, us_per_step);
     if (precision == SFM_FP32X2)
         return autotune_impl<sfm::PolF32x2>(h, nsteps, ncw, nstage, us_per_step);
+    if (precision == SFM_FP32F)
+        return autotune_impl<sfm::PolF32F>(h, nsteps, ncw, nstage, us_per_step);
     return fail(h, SFM_ERR_ARG, "sfm_autotune: unknown precision");
 }
 

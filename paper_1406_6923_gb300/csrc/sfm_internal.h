@@ -81,6 +81,13 @@ cudaError_t launch_pack_tiles(const double* master, const long long* master_off,
                               const long long* tile_off, const int* sub_b, const int* sub_k,
                               int nsub, typename P::S* out, cudaStream_t st);
 
+// FP64 masters -> FP32 lower Cholesky factors in 8x8 tiles (same offsets as
+// launch_pack_tiles); *bad is set if a block the stepping uses is not
+// positive definite.
+cudaError_t launch_factor_tiles(const double* master, const long long* master_off,
+                                const long long* tile_off, const int* sub_b, const int* sub_k,
+                                int nsub, int kmax, float* out, int* bad, cudaStream_t st);
+
 // number of 8x8 tiles kept of a b x b symmetric block (upper triangle of tiles)
 __host__ __device__ inline long long sym_tiles(int b) {
     const long long nt = (b + 7) / 8;

@@ -221,6 +221,67 @@ __device__ __forceinline__ void tile_row(const typename P::S* tiles, int nt, int
     if (q == 0) y[8 * I + r] = v;
 }
 
+// y = L (L^T x) for one S-fraction block held as its lower Cholesky factor
+// L in shared memory: lower-triangular 8x8 tiles (tile (I,J), J <= I, at
+// index I(I+1)/2 + J, row-major inside the tile, zero above the diagonal
+// and beyond b).  One warp does the whole block.  Lane (r, q) reads the two
+// consecutive elements (r, 2q), (r, 2q+1) of every tile (one conflict-free
+// 8-byte load per tile per pass):
+//   z = L^T x: lane sums x_{8I+r} L_IJ[r][2q..2q+1] over I >= J, then an
+//              xor butterfly over r leaves z_{8J+2q}, z_{8J+2q+1} in every
+//              lane of that q, which is what the second pass reads;
+//   y = L z:   lane sums L_IJ[r][2q..2q+1] . z_J[2q..2q+1] over J <= I, then
+//              a butterfly over q gives y_{8I+r}.
+// The summation order is fixed by (nt, lane), never by the block shape.
+// (Blocks up to 64 wide: the loops run to 8 tiles with uniform guards, one
+// instance for every width, which keeps the arrays in registers.)
+__device__ __forceinline__ void factor_mv(int nt, const float* tiles, const float* x, float* y) {
+    constexpr int NTMAX = 8;
+    const int lane = threadIdx.x & 31, r = lane >> 2, q = lane & 3;
+    const float* t0 = tiles + r * 8 + 2 * q;
+    float xr[NTMAX], z0[NTMAX], z1[NTMAX];
+#pragma unroll
+    for (int I = 0; I < NTMAX; ++I) xr[I] = (I < nt) ? x[8 * I + r] : 0.f;
+#pragma unroll
+    for (int J = 0; J < NTMAX; ++J) {
+        float a0 = 0.f, a1 = 0.f;
+        if (J < nt) {
+#pragma unroll
+            for (int I = J; I < NTMAX; ++I) {
+                if (I < nt) {
+                    const float2 l =
+                        *reinterpret_cast<const float2*>(t0 + (I * (I + 1) / 2 + J) * 64);
+                    a0 = fmaf(l.x, xr[I], a0);
+                    a1 = fmaf(l.y, xr[I], a1);
+                }
+            }
+#pragma unroll
+            for (int o = 4; o < 32; o <<= 1) {
+                a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+                a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+            }
+        }
+        z0[J] = a0;
+        z1[J] = a1;
+    }
+#pragma unroll
+    for (int I = 0; I < NTMAX; ++I) {
+        if (I < nt) {
+            float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+            for (int J = 0; J <= I; ++J) {
+                const float2 l = *reinterpret_cast<const float2*>(t0 + (I * (I + 1) / 2 + J) * 64);
+                a0 = fmaf(l.x, z0[J], a0);
+                a1 = fmaf(l.y, z1[J], a1);
+            }
+            float v = a0 + a1;
+            v += __shfl_xor_sync(0xffffffffu, v, 1);
+            v += __shfl_xor_sync(0xffffffffu, v, 2);
+            if (q == 0) y[8 * I + r] = v;
+        }
+    }
+}
+
 // Work of one block per time step: a list of pieces (unit, j0, j1), each a
 // contiguous range of levels of one (shot, subdomain) unit.  A piece streams
 // Gamma_j for j in [max(j0-1, 0), j1) (the extra level j0-1 gives phi_{j0-1},
@@ -251,7 +312,7 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
     if (threadIdx.x == 0) {
         for (int i = 0; i < nstage; ++i) {
             mbar_init(full + i, 1);
-            mbar_init(empty + i, ncw);
+            mbar_init(empty + i, P::factored ? 1 : ncw);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -261,6 +322,8 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
         // ------------------------------ producer ------------------------------
         if (lane != 0) return;
         long long g = 0;
+        int st = 0;            // stage of block g = g % nstage
+        unsigned ph = 0;       // parity of that stage's current use = (g / nstage) & 1
         bool ok = true;
         for (int n = 0; n < p.nsteps && ok; ++n) {
             for (int pc = pc0; pc < pc1 && ok; ++pc) {
@@ -274,9 +337,8 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
                 const int jl = j0 > 0 ? j0 - 1 : 0, ja = j0 > 1 ? j0 : 1;
                 const int nblk = piece_blocks(j0, j1);
                 for (int m = 0; m < nblk; ++m, ++g) {
-                    const int st = (int)(g % nstage);
-                    if (g >= nstage &&
-                        !mbar_wait(empty + st, (unsigned)((g / nstage - 1) & 1), p.err, p.timeout_ns)) {
+                    // the stage's previous use (block g - nstage) must be released
+                    if (g >= nstage && !mbar_wait(empty + st, ph ^ 1u, p.err, p.timeout_ns)) {
                         ok = false;
                         break;
                     }
@@ -284,6 +346,7 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
                                                         : T0 + (long long)(ja + m - (j1 - jl)) * ltile + ltile / 2;
                     mbar_expect_tx(full + st, bytes);
                     bulk_g2s(stages + (size_t)st * stage_elems, p.coef + off, bytes, full + st);
+                    if (++st == nstage) { st = 0; ph ^= 1u; }
                 }
             }
         }
@@ -295,7 +358,18 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
 
     // ------------------------------- consumers --------------------------------
     const C dt2 = P::from_d(p.dt2);
-    long long g = 0;   // running index of the streamed blocks (same order as the producer)
+    // Running position in the stream of blocks (same order as the producer):
+    // stage cst = g % nstage, parity cph = (g / nstage) & 1 of its use, and
+    // for factored blocks the owner warp own = g % ncw (ncw divides nstage,
+    // so every stage always has the same owner, which waits for each of its
+    // phases in order: a warp never waits on a stage more than one phase
+    // ahead of the producer).  A failed bounded wait marks the warp dead: it
+    // skips its remaining waits and arithmetic but keeps taking part in the
+    // block's named barriers, and the next device-wide barrier, which sees
+    // the error flag, sends every warp out together.
+    int cst = 0, own = 0;
+    unsigned cph = 0;
+    bool dead = false;
     for (int n = 0; n < p.nsteps; ++n) {
         const S* Ucur = p.U[n % 3];
         S* Unxt = p.U[(n + 1) % 3];
@@ -331,18 +405,33 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
             int task = 0;
             for (int half = 0; half < 2; ++half) {
                 const int lo = half ? ja : jl;
-                for (int j = lo; j < j1; ++j, ++g) {
-                    const int st = (int)(g % nstage);
-                    const int first = (warp - task % ncw + ncw) % ncw;
-                    if (!mbar_wait(full + st, (unsigned)((g / nstage) & 1), p.err, p.timeout_ns))
-                        return;
+                for (int j = lo; j < j1; ++j) {
+                    const int st = cst, owner = own;
+                    const unsigned ph = cph;
+                    if (++cst == nstage) { cst = 0; cph ^= 1u; }
+                    if (++own == ncw) own = 0;
                     const int lj = j - jl;
-                    for (int I = first; I < nt; I += ncw)
-                        tile_row<P>(stages + (size_t)st * stage_elems, nt, I, sD + lj * bp,
-                                    sPhi + lj * bp);
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(empty + st);
-                    task += nt;
+                    if constexpr (P::factored) {
+                        // factored blocks: one warp per block, in turn
+                        if (owner != warp) continue;
+                        if (!dead && !mbar_wait(full + st, ph, p.err, p.timeout_ns)) dead = true;
+                        if (dead) continue;
+                        factor_mv(nt, reinterpret_cast<const float*>(stages) + (size_t)st * stage_elems,
+                                  reinterpret_cast<const float*>(sD) + lj * bp,
+                                  reinterpret_cast<float*>(sPhi) + lj * bp);
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(empty + st);
+                    } else {
+                        const int first = (warp - task % ncw + ncw) % ncw;
+                        task += nt;
+                        if (!dead && !mbar_wait(full + st, ph, p.err, p.timeout_ns)) dead = true;
+                        if (dead) continue;
+                        for (int I = first; I < nt; I += ncw)
+                            tile_row<P>(stages + (size_t)st * stage_elems, nt, I, sD + lj * bp,
+                                        sPhi + lj * bp);
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(empty + st);
+                    }
                 }
                 cbar(nct);
                 if (half == 0) {
@@ -495,6 +584,7 @@ void build_pieces(int nunits, int nsub, const int* k_sub, int grid, std::vector<
 SFM_INST(PolF64)
 SFM_INST(PolF32)
 SFM_INST(PolF32x2)
+SFM_INST(PolF32F)
 #undef SFM_INST
 
 // ---------------------------------------------------------------------------
@@ -587,6 +677,73 @@ cudaError_t launch_pack_tiles(const double* master, const long long* master_off,
     return cudaGetLastError();
 }
 
+// Cholesky factors of the S-fraction blocks for the factored FP32 policy.
+// One block of threads per (subdomain, coefficient block): Gamma_j is block
+// 2j, Gammahat_j block 2j+1 (the level-major order of the packed tiles).
+// The b x b FP64 block is factored in shared memory (right-looking, column
+// by column, in FP64), then rounded to FP32 into lower-triangular 8x8 tiles.
+// A non-positive pivot in a block the stepping uses (every Gamma_j and
+// Gammahat_j for j >= 2) sets *bad; Gammahat_1 is replaced by H_f on the
+// faces and is not needed.
+constexpr int FAC_LD = 65;
+
+__global__ void __launch_bounds__(256) factor_tiles_kernel(const double* master,
+                                                           const long long* master_off,
+                                                           const long long* tile_off,
+                                                           const int* sub_b, const int* sub_k,
+                                                           float* out, int* bad) {
+    __shared__ double A[64 * FAC_LD];
+    const int s = blockIdx.y, blk = blockIdx.x;
+    const int b = sub_b[s], k = sub_k[s];
+    if (blk >= 2 * k) return;
+    const int j = blk >> 1, which = blk & 1;
+    const int nt = (b + 7) / 8, T = nt * (nt + 1) / 2;
+    const double* m = master + master_off[s] + ((long long)which * k + j) * b * b;
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) A[(e / b) * FAC_LD + e % b] = m[e];
+    bool ok = true;
+    for (int c = 0; c < b; ++c) {
+        __syncthreads();
+        const double d = A[c * FAC_LD + c];
+        if (!(d > 0.0)) { ok = false; break; }   // same value in every thread
+        const double l = sqrt(d);
+        __syncthreads();
+        if (threadIdx.x == 0) A[c * FAC_LD + c] = l;
+        for (int i = c + 1 + threadIdx.x; i < b; i += blockDim.x) A[i * FAC_LD + c] /= l;
+        __syncthreads();
+        const int n = b - c - 1;
+        for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+            const int i = c + 1 + t / n, jj = c + 1 + t % n;
+            if (jj <= i) A[i * FAC_LD + jj] -= A[i * FAC_LD + c] * A[jj * FAC_LD + c];
+        }
+    }
+    __syncthreads();
+    if (!ok) {
+        if (threadIdx.x == 0 && !(which == 1 && j == 0)) atomicExch(bad, 1);
+    }
+    float* o = out + tile_off[s] + (long long)blk * T * 64;
+    for (int e = threadIdx.x; e < T * 64; e += blockDim.x) {
+        const int tix = e >> 6, rc = e & 63;
+        int I = 0;
+        while ((I + 1) * (I + 2) / 2 <= tix) ++I;
+        const int J = tix - I * (I + 1) / 2;
+        const int row = 8 * I + (rc >> 3), col = 8 * J + (rc & 7);
+        const double v = (ok && row < b && col <= row) ? A[row * FAC_LD + col] : 0.0;
+        o[e] = __double2float_rn(v);
+    }
+}
+
+cudaError_t launch_factor_tiles(const double* master, const long long* master_off,
+                                const long long* tile_off, const int* sub_b, const int* sub_k,
+                                int nsub, int kmax, float* out, int* bad, cudaStream_t st) {
+    for (int s0 = 0; s0 < nsub; s0 += 65535) {
+        const int ns = nsub - s0 < 65535 ? nsub - s0 : 65535;
+        factor_tiles_kernel<<<dim3(2 * kmax, ns), 256, 0, st>>>(master, master_off + s0,
+                                                                tile_off + s0, sub_b + s0,
+                                                                sub_k + s0, out, bad);
+    }
+    return cudaGetLastError();
+}
+
 #define SFM_INST2(P)                                                                           \
     template cudaError_t launch_reduce_traces<P>(const P::S*, const int*, const int*, int, int, \
                                                  int, int, double*, int*, cudaStream_t);       \
@@ -596,6 +753,7 @@ cudaError_t launch_pack_tiles(const double* master, const long long* master_off,
 SFM_INST2(PolF64)
 SFM_INST2(PolF32)
 SFM_INST2(PolF32x2)
+SFM_INST2(PolF32F)
 #undef SFM_INST2
 
 // ---------------------------------------------------------------------------

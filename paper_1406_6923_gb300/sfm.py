@@ -27,6 +27,7 @@ SFM_ERR_STATE = -8
 SFM_FP64 = 0
 SFM_FP32 = 1
 SFM_FP32X2 = 2
+SFM_FP32F = 3
 
 SFM_DEVICE_PTR = 1
 
