@@ -167,7 +167,7 @@ int sfm_cfl_dt(sfm_handle* h, int iters, double* lambda_max, double* dt_cfl);
 /*
  * Shape search for the stepping kernel of `precision` on this handle (no
  * counterpart in the paper, whose method fixes no launch shape).  Each
- * candidate block shape - consumer warps in {2,4,6,8,12,16} times
+ * candidate block shape - consumer warps in {2,4,6,8} times
  * coefficient ring stages in {2,3,4,6,8,12,16}, those whose shared memory
  * fits (for SFM_FP32F only stage counts that are multiples of the warps) -
  * steps the coupled system `nsteps` steps from a zero source twice; the
@@ -291,7 +291,7 @@ int sfm_last_launches(const sfm_handle* h, int* launches);
  *   key 2: index of a block that skips its barrier arrivals (-1 = none), so
  *          that every block's bounded wait runs out and sfm_run returns
  *          SFM_ERR_TIMEOUT with the context still usable;
- *   key 3: consumer warps per stepping block (1..16), all precisions;
+ *   key 3: consumer warps per stepping block (1..8), all precisions;
  *   key 4: coefficient ring stages per stepping block (2..16), all
  *          precisions (keys 3 and 4 override sfm_autotune's choice; for
  *          SFM_FP32F the stages are rounded up to a multiple of the warps).

@@ -399,7 +399,7 @@ int sfm_debug_set(sfm_handle* h, int key, long long value) {
     if (key == 1) { ext(h)->timeout_ns = (unsigned long long)value; return SFM_OK; }
     if (key == 2) { ext(h)->skip_arrive = (int)value; return SFM_OK; }
     if (key == 3) {
-        if (value < 1 || value > 16) return fail(h, SFM_ERR_ARG, "sfm_debug_set: consumer warps 1..16");
+        if (value < 1 || value > 8) return fail(h, SFM_ERR_ARG, "sfm_debug_set: consumer warps 1..8");
         for (int i = 0; i < 4; ++i) ext(h)->ncw[i] = (int)value;
         return SFM_OK;
     }
@@ -635,7 +635,7 @@ extern "C" int sfm_run(sfm_handle* h, int precision, double dt, int nsteps, cons
 // can go unstable, and the timing does not depend on the values.
 template <class P>
 static int autotune_impl(sfm_handle* h, int nsteps, int* ncw_out, int* nstage_out, double* us_out) {
-    static const int kNcw[] = {2, 4, 6, 8, 12, 16};
+    static const int kNcw[] = {2, 4, 6, 8};
     static const int kStage[] = {2, 3, 4, 6, 8, 12, 16};
     sfm_ext* x = ext(h);
     const int id = prec_id(P{});

@@ -48,7 +48,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // arithmetic, one producer warp streams the coefficient blocks into shared
 // memory with bulk asynchronous copies (the TMA engine) through a ring of
 // p.nstage stages.  Both are chosen at launch (see step_config).
-constexpr int NCW_MAX = 16;
+constexpr int NCW_MAX = 8;
 constexpr int STEP_BLOCK_MAX = (NCW_MAX + 1) * 32;
 
 __device__ __forceinline__ void cbar(int nct) {
@@ -91,14 +91,16 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
                                           unsigned long long timeout_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
-    while (!mbar_try_wait(bar, parity)) {
-        if (*(volatile int*)err != 0) return false;
-        if (global_ns() - t0 > timeout_ns) {
-            atomicCAS(err, 0, (int)SFM_ERR_TIMEOUT);
-            return false;
+    for (unsigned it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 7) == 0) {   // the error flag and the clock every 8 polls
+            if (*(volatile int*)err != 0) return false;
+            if (global_ns() - t0 > timeout_ns) {
+                atomicCAS(err, 0, (int)SFM_ERR_TIMEOUT);
+                return false;
+            }
         }
     }
-    return true;
 }
 
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
@@ -107,6 +109,20 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
         ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
+}
+
+// Per-thread asynchronous global -> shared copies (4 or 8 bytes): a block
+// issues all copies of a piece, then waits once, instead of paying the load
+// latency once per loop trip.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src),
+                 "n"(BYTES)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // Bounded device-wide barrier among the consumer threads of every block.
@@ -167,6 +183,7 @@ __device__ void readout(const StepParams<typename P::S>& p, const typename P::S*
         const typename P::S* U = Ubuf + q * p.state_stride + p.state_off[s];
         typename P::Acc a0 = P::acc0(), a1 = P::acc0();
         int t = lane;
+#pragma unroll 4
         for (; t + 32 < kb; t += 64) {
             P::fma(a0, P::ld(row + t), P::ld(U + t));
             P::fma(a1, P::ld(row + t + 32), P::ld(U + t + 32));
@@ -233,15 +250,18 @@ __device__ __forceinline__ void tile_row(const typename P::S* tiles, int nt, int
 //   y = L z:   lane sums L_IJ[r][2q..2q+1] . z_J[2q..2q+1] over J <= I, then
 //              a butterfly over q gives y_{8I+r}.
 // The summation order is fixed by (nt, lane), never by the block shape.
-// (Blocks up to 64 wide: the loops run to 8 tiles with uniform guards, one
-// instance for every width, which keeps the arrays in registers.)
-__device__ __forceinline__ void factor_mv(int nt, const float* tiles, const float* x, float* y) {
+// xf(row) gives x at a row index 8I+r (read by the lanes of that r), ef(row,
+// y) receives the result in the four lanes q = 0 of each row group.  Blocks
+// up to 64 wide: the loops run to 8 tiles with uniform guards, one instance
+// for every width, which keeps the arrays in registers.
+template <class XF, class EF>
+__device__ __forceinline__ void factor_apply(int nt, const float* tiles, XF xf, EF ef) {
     constexpr int NTMAX = 8;
     const int lane = threadIdx.x & 31, r = lane >> 2, q = lane & 3;
     const float* t0 = tiles + r * 8 + 2 * q;
     float xr[NTMAX], z0[NTMAX], z1[NTMAX];
 #pragma unroll
-    for (int I = 0; I < NTMAX; ++I) xr[I] = (I < nt) ? x[8 * I + r] : 0.f;
+    for (int I = 0; I < NTMAX; ++I) xr[I] = (I < nt) ? xf(8 * I + r) : 0.f;
 #pragma unroll
     for (int J = 0; J < NTMAX; ++J) {
         float a0 = 0.f, a1 = 0.f;
@@ -277,9 +297,67 @@ __device__ __forceinline__ void factor_mv(int nt, const float* tiles, const floa
             float v = a0 + a1;
             v += __shfl_xor_sync(0xffffffffu, v, 1);
             v += __shfl_xor_sync(0xffffffffu, v, 2);
-            if (q == 0) y[8 * I + r] = v;
+            if (q == 0) ef(8 * I + r, v);
         }
     }
+}
+
+// The same product for a fixed tile count: no guards, so the compiler can
+// interleave the independent reductions of the tile columns and rows.
+template <int NT, class XF, class EF>
+__device__ __forceinline__ void factor_apply_nt(const float* tiles, XF xf, EF ef) {
+    const int lane = threadIdx.x & 31, r = lane >> 2, q = lane & 3;
+    const float* t0 = tiles + r * 8 + 2 * q;
+    float xr[NT], z0[NT], z1[NT];
+#pragma unroll
+    for (int I = 0; I < NT; ++I) xr[I] = xf(8 * I + r);
+#pragma unroll
+    for (int J = 0; J < NT; ++J) {
+        float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+        for (int I = J; I < NT; ++I) {
+            const float2 l = *reinterpret_cast<const float2*>(t0 + (I * (I + 1) / 2 + J) * 64);
+            a0 = fmaf(l.x, xr[I], a0);
+            a1 = fmaf(l.y, xr[I], a1);
+        }
+        z0[J] = a0;
+        z1[J] = a1;
+    }
+#pragma unroll
+    for (int o = 4; o < 32; o <<= 1) {
+#pragma unroll
+        for (int J = 0; J < NT; ++J) {
+            z0[J] += __shfl_xor_sync(0xffffffffu, z0[J], o);
+            z1[J] += __shfl_xor_sync(0xffffffffu, z1[J], o);
+        }
+    }
+    float v[NT];
+#pragma unroll
+    for (int I = 0; I < NT; ++I) {
+        float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+        for (int J = 0; J <= I; ++J) {
+            const float2 l = *reinterpret_cast<const float2*>(t0 + (I * (I + 1) / 2 + J) * 64);
+            a0 = fmaf(l.x, z0[J], a0);
+            a1 = fmaf(l.y, z1[J], a1);
+        }
+        v[I] = a0 + a1;
+    }
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+#pragma unroll
+        for (int I = 0; I < NT; ++I) v[I] += __shfl_xor_sync(0xffffffffu, v[I], o);
+    }
+    if (q == 0) {
+#pragma unroll
+        for (int I = 0; I < NT; ++I) ef(8 * I + r, v[I]);
+    }
+}
+
+template <class XF, class EF>
+__device__ __forceinline__ void factor_apply_any(int nt, const float* tiles, XF xf, EF ef) {
+    if (nt == 6) factor_apply_nt<6>(tiles, xf, ef);
+    else factor_apply(nt, tiles, xf, ef);
 }
 
 // Work of one block per time step: a list of pieces (unit, j0, j1), each a
@@ -390,12 +468,87 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
             const long long sof = p.src_off[(long long)q * p.nsub + s];
             const C w = P::ld(p.wavelet + (long long)q * p.nsteps + n);
             cbar(nct);
-            // padded copies of levels jl..j1 (local index = level - jl)
-            for (int t = threadIdx.x; t < (nl + 1) * bp; t += nct) {
-                const int lj = t / bp, i = t - lj * bp, j = jl + lj;
-                sU[t] = (j < k && i < b) ? P::ld(Uc + j * b + i) : P::zero();
+            // padded copies of levels jl..j1 (local index = level - jl), one
+            // level per warp, lanes along the level
+            static_assert(sizeof(C) == sizeof(S), "state copies are byte copies");
+            for (int lj = warp; lj <= nl; lj += ncw) {
+                const int j = jl + lj;
+                for (int i = lane; i < bp; i += 32) {
+                    if (j < k && i < b) cp_async<sizeof(S)>(sU + lj * bp + i, Uc + j * b + i);
+                    else sU[lj * bp + i] = P::zero();
+                }
             }
+            if constexpr (P::factored) {
+                // the increments of the updated levels, staged in sD
+                for (int lj = ja - jl + warp; lj < nl; lj += ncw) {
+                    const int j = jl + lj;
+                    for (int i = lane; i < b; i += 32) cp_async<sizeof(S)>(sD + lj * bp + i, dU + j * b + i);
+                }
+            }
+            cp_async_wait_all();
             cbar(nct);
+            if constexpr (P::factored) {
+                // One warp per streamed block (the owner of its stage).  The
+                // Gamma_j owner forms Delta_j = U_{j+1} - U_j as it loads it
+                // and leaves phi_j = L L^T Delta_j in sPhi; after the barrier
+                // the Gammahat_j owner forms psi_j = phi_j - phi_{j-1} + p_j f
+                // the same way and applies the increment update (Eq. 19) to
+                // its rows directly from the matvec.
+                const float* src = (sof >= 0) ? reinterpret_cast<const float*>(p.src) + sof : nullptr;
+                const float wf = (float)w;
+                for (int half = 0; half < 2; ++half) {
+                    const int lo = half ? ja : jl;
+                    for (int j = lo; j < j1; ++j) {
+                        const int st = cst, owner = own;
+                        const unsigned ph = cph;
+                        if (++cst == nstage) { cst = 0; cph ^= 1u; }
+                        if (++own == ncw) own = 0;
+                        if (owner != warp) continue;
+                        if (!dead && !mbar_wait(full + st, ph, p.err, p.timeout_ns)) dead = true;
+                        if (dead) continue;
+                        const float* tl = reinterpret_cast<const float*>(stages) + (size_t)st * stage_elems;
+                        const float* fU = reinterpret_cast<const float*>(sU) + (j - jl) * bp;
+                        float* fP = reinterpret_cast<float*>(sPhi) + (j - jl) * bp;
+                        if (half == 0) {
+                            factor_apply_any(nt, tl,
+                                         [&](int row) { return fU[bp + row] - fU[row]; },
+                                         [&](int row, float v) { fP[row] = v; });
+                        } else {
+                            const float* sj = src ? src + j * b : nullptr;
+                            const float* fD = reinterpret_cast<const float*>(sD) + (j - jl) * bp;
+                            float* dUj = reinterpret_cast<float*>(dU) + j * b;
+                            float* Unj = reinterpret_cast<float*>(Un) + j * b;
+                            const float d2 = (float)dt2;
+                            factor_apply_any(nt, tl,
+                                         [&](int row) {
+                                             float v = fP[row] - fP[row - bp];
+                                             if (sj && row < b) v += sj[row] * wf;
+                                             return v;
+                                         },
+                                         [&](int row, float v) {
+                                             if (row < b) {
+                                                 const float d = fD[row] + d2 * v;
+                                                 dUj[row] = d;
+                                                 Unj[row] = fU[row] + d;
+                                             }
+                                         });
+                        }
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(empty + st);
+                    }
+                    if (half == 0) {
+                        cbar(nct);
+                        // (2.1) publish face data [phi_1 + p_1 f]
+                        if (j0 == 0) {
+                            S* my_mail = mail + q * p.mail_stride + p.mail_off[s];
+                            for (int i = threadIdx.x; i < b; i += nct) {
+                                const C srcv = (sof >= 0) ? P::mul(P::ld(p.src + sof + i), w) : P::zero();
+                                P::st(my_mail + i, P::add(sPhi[i], srcv));
+                            }
+                        }
+                    }
+                }
+            } else {
             for (int t = threadIdx.x; t < nl * bp; t += nct) sD[t] = P::sub(sU[t + bp], sU[t]);
             cbar(nct);
             // phi_j = Gamma_j Delta_j for levels jl..j1-1, then after psi,
@@ -406,32 +559,19 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
             for (int half = 0; half < 2; ++half) {
                 const int lo = half ? ja : jl;
                 for (int j = lo; j < j1; ++j) {
-                    const int st = cst, owner = own;
+                    const int st = cst;
                     const unsigned ph = cph;
                     if (++cst == nstage) { cst = 0; cph ^= 1u; }
-                    if (++own == ncw) own = 0;
                     const int lj = j - jl;
-                    if constexpr (P::factored) {
-                        // factored blocks: one warp per block, in turn
-                        if (owner != warp) continue;
-                        if (!dead && !mbar_wait(full + st, ph, p.err, p.timeout_ns)) dead = true;
-                        if (dead) continue;
-                        factor_mv(nt, reinterpret_cast<const float*>(stages) + (size_t)st * stage_elems,
-                                  reinterpret_cast<const float*>(sD) + lj * bp,
-                                  reinterpret_cast<float*>(sPhi) + lj * bp);
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(empty + st);
-                    } else {
-                        const int first = (warp - task % ncw + ncw) % ncw;
-                        task += nt;
-                        if (!dead && !mbar_wait(full + st, ph, p.err, p.timeout_ns)) dead = true;
-                        if (dead) continue;
-                        for (int I = first; I < nt; I += ncw)
-                            tile_row<P>(stages + (size_t)st * stage_elems, nt, I, sD + lj * bp,
-                                        sPhi + lj * bp);
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(empty + st);
-                    }
+                    const int first = (warp - task % ncw + ncw) % ncw;
+                    task += nt;
+                    if (!dead && !mbar_wait(full + st, ph, p.err, p.timeout_ns)) dead = true;
+                    if (dead) continue;
+                    for (int I = first; I < nt; I += ncw)
+                        tile_row<P>(stages + (size_t)st * stage_elems, nt, I, sD + lj * bp,
+                                    sPhi + lj * bp);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(empty + st);
                 }
                 cbar(nct);
                 if (half == 0) {
@@ -443,21 +583,26 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
                             P::st(my_mail + i, P::add(sPhi[i], srcv));
                         }
                     }
-                    for (int t = threadIdx.x; t < (j1 - ja) * b; t += nct) {
-                        const int j = ja + t / b, i = t % b, lj = j - jl;
-                        const C srcv = (sof >= 0) ? P::mul(P::ld(p.src + sof + j * b + i), w) : P::zero();
-                        sD[lj * bp + i] = P::add(P::sub(sPhi[lj * bp + i], sPhi[(lj - 1) * bp + i]), srcv);
+                    for (int lj = ja - jl + warp; lj < nl; lj += ncw) {
+                        const int j = jl + lj;
+                        for (int i = lane; i < b; i += 32) {
+                            const C srcv = (sof >= 0) ? P::mul(P::ld(p.src + sof + j * b + i), w) : P::zero();
+                            sD[lj * bp + i] = P::add(P::sub(sPhi[lj * bp + i], sPhi[(lj - 1) * bp + i]), srcv);
+                        }
                     }
                     cbar(nct);
                 }
             }
             // (2.2) interior update of levels ja..j1-1, Eq. (19)
-            for (int t = threadIdx.x; t < (j1 - ja) * b; t += nct) {
-                const int j = ja + t / b, i = t % b, lj = j - jl;
-                if (p.Kx) P::st(p.Kx + so + j * b + i, sD[lj * bp + i]);
-                const C d = P::add(P::ld(dU + j * b + i), P::mul(dt2, sPhi[lj * bp + i]));
-                P::st(dU + j * b + i, d);
-                P::st(Un + j * b + i, P::add(sU[lj * bp + i], d));
+            for (int lj = ja - jl + warp; lj < nl; lj += ncw) {
+                const int j = jl + lj;
+                for (int i = lane; i < b; i += 32) {
+                    if (p.Kx) P::st(p.Kx + so + j * b + i, sD[lj * bp + i]);
+                    const C d = P::add(P::ld(dU + j * b + i), P::mul(dt2, sPhi[lj * bp + i]));
+                    P::st(dU + j * b + i, d);
+                    P::st(Un + j * b + i, P::add(sU[lj * bp + i], d));
+                }
+            }
             }
         }
 
