@@ -98,8 +98,8 @@ struct sfm_ext {
     // warps and coefficient ring stages; sfm_autotune overwrites these
     int ncw[4] = {8, 8, 8, 8}, nstage[4] = {4, 4, 4, 4};
     int* d_piece_ptr = nullptr;
-    int4* d_pieces = nullptr;
-    int piece_grid = -1, piece_units = -1;
+    int4* d_prec = nullptr;            // piece records (sfm::piece_records)
+    int piece_grid = -1, piece_units = -1, piece_src = -1;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
@@ -151,7 +151,7 @@ int sfm_destroy(sfm_handle* h) {
     if (x) {
         x->c32.release(); x->c64.release(); x->c2.release(); x->c32f.release();
         x->r32.release(); x->r64.release(); x->r2.release();
-        dfree(x->d_traces); dfree(x->d_bad); dfree(x->d_piece_ptr); dfree(x->d_pieces);
+        dfree(x->d_traces); dfree(x->d_bad); dfree(x->d_piece_ptr); dfree(x->d_prec);
         if (x->ev0) cudaEventDestroy(x->ev0);
         if (x->ev1) cudaEventDestroy(x->ev1);
         delete x;
@@ -162,6 +162,7 @@ int sfm_destroy(sfm_handle* h) {
     dfree(h->d_tcoef_off);
     dfree(h->d_coef64); dfree(h->d_H64); dfree(h->d_src64); dfree(h->d_src_off);
     dfree(h->d_rrows64); dfree(h->d_rp_sub); dfree(h->d_rec_ptr); dfree(h->d_rec_pairs);
+    dfree(h->d_frow); dfree(h->d_rtab);
     dfree(h->d_rp_off); dfree(h->d_bar); dfree(h->d_err);
     if (h->stream && h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -258,6 +259,13 @@ int sfm_set_topology(sfm_handle* h, int nsub, const int* k_sub, const int* m_fac
     CK(h, upload(h->d_H_off, h->H_off.data(), 6 * (size_t)nsub, st));
     CK(h, upload(h->d_state_off, h->state_off.data(), nsub, st));
     CK(h, upload(h->d_mail_off, h->mail_off.data(), nsub, st));
+    {
+        std::vector<int4> rows;
+        if (!sfm::face_rows(nsub, h->b.data(), h->face_off.data(), h->nbr.data(), h->H_off.data(),
+                            h->mail_off.data(), rows))
+            return fail(h, SFM_ERR_ARG, "sfm_set_topology: offsets beyond 32 bits");
+        CK(h, upload(h->d_frow, rows.data(), rows.size(), st));
+    }
     h->have_coef = h->have_src = h->have_rec = false;
     invalidate(h);
     return SFM_OK;
@@ -355,6 +363,7 @@ int sfm_set_sources(sfm_handle* h, int nshots, int npairs, const int* pair_shot,
     CK(h, upload(h->d_src64, rows, (size_t)o, h->stream));
     CK(h, upload(h->d_src_off, off.data(), off.size(), h->stream));
     h->have_src = true;
+    ext(h)->piece_grid = -1;   // piece records carry the source offsets
     invalidate(h);
     return SFM_OK;
 }
@@ -387,6 +396,13 @@ int sfm_set_receivers(sfm_handle* h, int nrec, int npairs, const int* pair_rec,
     CK(h, upload(h->d_rrows64, rows, (size_t)o, st));
     CK(h, upload(h->d_rp_sub, rsub.data(), rsub.size(), st));
     CK(h, upload(h->d_rp_off, roff.data(), roff.size(), st));
+    {
+        std::vector<int4> tab;
+        if (!sfm::readout_table((int)rsub.size(), rsub.data(), roff.data(), h->k.data(), h->b.data(),
+                                h->state_off.data(), tab))
+            return fail(h, SFM_ERR_ARG, "sfm_set_receivers: offsets beyond 32 bits");
+        CK(h, upload(h->d_rtab, tab.data(), tab.size(), st));
+    }
     CK(h, upload(h->d_rec_ptr, cnt.data(), cnt.size(), st));
     CK(h, upload(h->d_rec_pairs, pairs.data(), pairs.size(), st));
     h->have_rec = true;
@@ -474,8 +490,10 @@ static int prec_id(sfm::PolF32F) { return SFM_FP32F; }
 
 // Grid of the persistent stepping kernel (co-resident blocks for the
 // chosen shape, at most one per level of work) and the per-block pieces.
+// src_off: host source offsets per (shot, subdomain), NULL for none (kind 0).
 template <class P>
-static int step_setup(sfm_handle* h, int nunits, sfm::StepParams<typename P::S>& p, int* grid_out) {
+static int step_setup(sfm_handle* h, int nunits, const long long* src_off,
+                      sfm::StepParams<typename P::S>& p, int* grid_out) {
     sfm_ext* x = ext(h);
     const int id = prec_id(P{});
     const int ncw = x->ncw[id];
@@ -489,19 +507,27 @@ static int step_setup(sfm_handle* h, int nunits, sfm::StepParams<typename P::S>&
     long long levels = 0;
     for (int u = 0; u < nunits; ++u) levels += h->k[u % h->nsub];
     const int grid = (int)std::max(1LL, std::min<long long>(gmax, levels));
-    if (grid != x->piece_grid || nunits != x->piece_units) {
+    const int src_kind = src_off ? 1 : 0;
+    if (grid != x->piece_grid || nunits != x->piece_units || src_kind != x->piece_src) {
         std::vector<int> ptr;
-        std::vector<int4> pieces;
+        std::vector<int4> pieces, rec;
         sfm::build_pieces(nunits, h->nsub, h->k.data(), grid, ptr, pieces);
+        std::vector<long long> none;
+        if (!src_off) { none.assign((size_t)nunits, -1); src_off = none.data(); }
+        if (!sfm::piece_records(pieces, h->nsub, h->k.data(), h->b.data(), h->state_off.data(),
+                                src_off, h->mail_off.data(), rec))
+            return fail(h, SFM_ERR_ARG, "stepping: offsets beyond 32 bits");
         CK(h, upload(x->d_piece_ptr, ptr.data(), ptr.size(), h->stream));
-        CK(h, upload(x->d_pieces, pieces.data(), pieces.size(), h->stream));
+        CK(h, upload(x->d_prec, rec.data(), rec.size(), h->stream));
         x->piece_grid = grid;
         x->piece_units = nunits;
+        x->piece_src = src_kind;
     }
     p.ncw = ncw;
     p.nstage = nstage;
     p.piece_ptr = x->d_piece_ptr;
-    p.pieces = x->d_pieces;
+    p.prec = x->d_prec;
+    p.frow = h->d_frow;
     *grid_out = grid;
     return SFM_OK;
 }
@@ -577,7 +603,8 @@ static int run_impl(sfm_handle* h, double dt, int nsteps, const double* wavelet,
     p.Kx = nullptr;
 
     int grid = 0;
-    rc = step_setup<P>(h, p.nunits, p, &grid);
+    rc = step_setup<P>(h, p.nunits, h->src_off.data(), p, &grid);
+    p.rtab = h->d_rtab;
     if (rc != SFM_OK) { dfree(tmp64); return rc; }
     CK(h, cudaEventRecord(x->ev0, st));
     cudaError_t e = sfm::launch_step<P>(p, grid, st);
@@ -783,7 +810,7 @@ extern "C" int sfm_cfl_dt(sfm_handle* h, int iters, double* lambda_max, double* 
     p.Kx = Kx;
     int grid = 0;
     {
-        const int r2 = step_setup<sfm::PolF64>(h, h->nsub, p, &grid);
+        const int r2 = step_setup<sfm::PolF64>(h, h->nsub, nullptr, p, &grid);
         if (r2 != SFM_OK) { cleanup(); return r2; }
     }
     auto apply = [&](const double* in) -> cudaError_t {

@@ -54,7 +54,9 @@ struct StepParams {
                                  // blocks are applied), state layout; NULL when stepping
     int ncw, nstage;             // consumer warps per block, shared-memory ring stages
     const int* piece_ptr;        // [grid+1] pieces of each block
-    const int4* pieces;          // (unit, j0, j1, -): levels [j0, j1) of a unit
+    const int4* prec;            // [2*npieces] piece records (see piece_records)
+    const int4* frow;            // [mail layout] face rows (see face_rows)
+    const int4* rtab;            // [nrpairs] receiver pairs (see readout_table)
 };
 
 // launchers (step.cu); P is a number policy of numeric.cuh
@@ -66,6 +68,13 @@ template <class P>
 size_t step_smem_bytes(int kmax, int bmax, int nstage);
 void build_pieces(int nunits, int nsub, const int* k_sub, int grid, std::vector<int>& ptr,
                   std::vector<int4>& pieces);
+bool piece_records(const std::vector<int4>& pieces, int nsub, const int* k, const int* b,
+                   const long long* state_off, const long long* src_off, const long long* mail_off,
+                   std::vector<int4>& rec);
+bool face_rows(int nsub, const int* b, const int* face_off, const int* nbr,
+               const long long* H_off, const long long* mail_off, std::vector<int4>& rows);
+bool readout_table(int nrpairs, const int* rp_sub, const long long* rp_off, const int* k,
+                   const int* b, const long long* state_off, std::vector<int4>& tab);
 
 cudaError_t launch_face_H(const double* coef, const long long* gh1_off, const int* sub_b,
                           const int* face_off, const int* nbr, const long long* H_off,
@@ -152,6 +161,8 @@ struct sfm_handle {
     double* d_rrows64 = nullptr;
     int *d_rp_sub = nullptr, *d_rec_ptr = nullptr, *d_rec_pairs = nullptr;
     long long* d_rp_off = nullptr;
+    int4* d_frow = nullptr;            // face rows (face_rows), set with the topology
+    int4* d_rtab = nullptr;            // receiver pair table (readout_table)
     bool have_src = false, have_rec = false;
 
     // offline builder state (builder.cu), NULL until sfm_set_model

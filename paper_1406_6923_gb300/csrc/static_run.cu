@@ -137,11 +137,18 @@ extern "C" int sfm_run_static(int device, void* stream, int nsub, const int* k_s
     for (int u = 0; u < nshots * nsub; ++u) levels += k_sub[u % nsub];
     const int grid = (int)std::max(1LL, std::min<long long>(gmax, levels));
     std::vector<int> piece_ptr;
-    std::vector<int4> pieces;
+    std::vector<int4> pieces, prec, frow, rtab;
     sfm::build_pieces(nshots * nsub, nsub, k_sub, grid, piece_ptr, pieces);
+    if (!sfm::piece_records(pieces, nsub, k_sub, b.data(), state_off.data(), src_off.data(),
+                            mail_off.data(), prec) ||
+        !sfm::face_rows(nsub, b.data(), face_off.data(), nb.data(), H_off.data(), mail_off.data(), frow) ||
+        !sfm::readout_table(nrec_pairs, rp_sub.data(), rp_off.data(), k_sub, b.data(),
+                            state_off.data(), rtab))
+        return sfail(SFM_ERR_ARG, "sfm_run_static: offsets beyond 32 bits");
     // ---- carve the scratch array ----
     Carve cv;
-    const size_t o_pp = cv.take<int>(piece_ptr.size()), o_pc = cv.take<int4>(pieces.size());
+    const size_t o_pp = cv.take<int>(piece_ptr.size()), o_pc = cv.take<int4>(prec.size()),
+                 o_fr = cv.take<int4>(frow.size()), o_rt = cv.take<int4>(rtab.size());
     const size_t o_b = cv.take<int>(nsub), o_k = cv.take<int>(nsub), o_fo = cv.take<int>(7 * (size_t)nsub),
                  o_nb = cv.take<int>(6 * (size_t)nsub), o_ho = cv.take<long long>(6 * (size_t)nsub),
                  o_to = cv.take<long long>(nsub), o_co = cv.take<long long>(nsub),
@@ -191,7 +198,9 @@ extern "C" int sfm_run_static(int device, void* stream, int nsub, const int* k_s
     SCK(put(o_rp, cnt.data(), cnt.size() * sizeof(int)));
     SCK(put(o_pr, pairs.data(), pairs.size() * sizeof(int)));
     SCK(put(o_pp, piece_ptr.data(), piece_ptr.size() * sizeof(int)));
-    SCK(put(o_pc, pieces.data(), pieces.size() * sizeof(int4)));
+    SCK(put(o_pc, prec.data(), prec.size() * sizeof(int4)));
+    SCK(put(o_fr, frow.data(), frow.size() * sizeof(int4)));
+    SCK(put(o_rt, rtab.data(), rtab.size() * sizeof(int4)));
     auto at = [&](size_t off) { return (void*)(base + off); };
     // every call shares the array: clear what has to start at zero
     for (auto u : o_U) SCK(cudaMemsetAsync(at(u), 0, (size_t)nshots * so * sizeof(double), st));
@@ -225,7 +234,8 @@ extern "C" int sfm_run_static(int device, void* stream, int nsub, const int* k_s
     p.bar = (unsigned int*)at(o_bar); p.err = (int*)at(o_err);
     p.timeout_ns = 2000000000ull; p.skip_arrive = -1; p.Kx = nullptr;
     p.ncw = ncw; p.nstage = nstage;
-    p.piece_ptr = (const int*)at(o_pp); p.pieces = (const int4*)at(o_pc);
+    p.piece_ptr = (const int*)at(o_pp); p.prec = (const int4*)at(o_pc);
+    p.frow = (const int4*)at(o_fr); p.rtab = (const int4*)at(o_rt);
     SCK(sfm::launch_step<P>(p, grid, st));
     SCK(sfm::launch_reduce_traces<P>((const double*)at(o_part), (const int*)at(o_rp), (const int*)at(o_pr),
                                      nshots, nsteps, nrec, nrec_pairs, traces, (int*)at(o_bad), st));

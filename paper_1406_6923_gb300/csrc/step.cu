@@ -25,6 +25,8 @@
 #include "sfm_internal.h"
 
 #include <cooperative_groups.h>
+#include <climits>
+#include <algorithm>
 
 namespace sfm {
 
@@ -176,11 +178,11 @@ __device__ void readout(const StepParams<typename P::S>& p, const typename P::S*
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (long long it = (long long)blockIdx.x * p.ncw + warp; it < items;
          it += (long long)gridDim.x * p.ncw) {
-        const int q = (int)(it / p.nrpairs), r = (int)(it % p.nrpairs);
-        const int s = p.rp_sub[r];
-        const int kb = p.sub_k[s] * p.sub_b[s];
-        const typename P::S* row = p.rrows + p.rp_off[r];
-        const typename P::S* U = Ubuf + q * p.state_stride + p.state_off[s];
+        const int q = (int)(it / p.nrpairs), r = (int)(it - (long long)q * p.nrpairs);
+        const int4 e = p.rtab[r];
+        const int kb = e.x;
+        const typename P::S* row = p.rrows + e.y;
+        const typename P::S* U = Ubuf + q * p.state_stride + e.z;
         typename P::Acc a0 = P::acc0(), a1 = P::acc0();
         int t = lane;
 #pragma unroll 4
@@ -381,8 +383,10 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
     C* sU = reinterpret_cast<C*>(stages + (size_t)nstage * stage_elems);   // (kmax+1)*bpm
     C* sD = sU + (p.kmax + 1) * bpm;                     // kmax*bpm: Delta, then psi
     C* sPhi = sD + p.kmax * bpm;                         // kmax*bpm: phi, then a
+    C* sSrc = sPhi + p.kmax * bpm;                       // kmax*bpm: source rows (factored)
+    C* sEnd = P::factored ? sSrc + p.kmax * bpm : sSrc;
     unsigned long long* full = reinterpret_cast<unsigned long long*>(
-        (reinterpret_cast<uintptr_t>(sPhi + p.kmax * bpm) + 15) & ~(uintptr_t)15);
+        (reinterpret_cast<uintptr_t>(sEnd) + 15) & ~(uintptr_t)15);
     unsigned long long* empty = full + nstage;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int pc0 = p.piece_ptr[blockIdx.x], pc1 = p.piece_ptr[blockIdx.x + 1];
@@ -405,9 +409,9 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
         bool ok = true;
         for (int n = 0; n < p.nsteps && ok; ++n) {
             for (int pc = pc0; pc < pc1 && ok; ++pc) {
-                const int4 pe = p.pieces[pc];
-                const int s = pe.x % p.nsub, j0 = pe.y, j1 = pe.z;
-                const int b = p.sub_b[s];
+                const int4 r0 = p.prec[2 * pc], r1 = p.prec[2 * pc + 1];
+                const int s = r0.y, j0 = r0.z, j1 = r0.w;
+                const int b = r1.x & 255;
                 const int nt = (b + 7) >> 3;
                 const long long ltile = 2LL * (nt * (nt + 1) / 2) * 64;
                 const unsigned bytes = (unsigned)((ltile / 2) * sizeof(S));
@@ -455,17 +459,17 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
 
         // ---------------- phase A ----------------
         for (int pc = pc0; pc < pc1; ++pc) {
-            const int4 pe = p.pieces[pc];
-            const int u = pe.x, j0 = pe.y, j1 = pe.z;
-            const int q = u / p.nsub, s = u - q * p.nsub;
-            const int b = p.sub_b[s], k = p.sub_k[s];
+            const int4 r0 = p.prec[2 * pc], r1 = p.prec[2 * pc + 1];
+            const int q = r0.x, j0 = r0.z, j1 = r0.w;
+            const int b = r1.x & 255, k = r1.x >> 8;
             const int nt = (b + 7) >> 3, bp = nt * 8;
             const int jl = j0 > 0 ? j0 - 1 : 0, ja = j0 > 1 ? j0 : 1, nl = j1 - jl;
-            const long long so = q * p.state_stride + p.state_off[s];
+            const long long so = q * p.state_stride + r1.y;
             const S* Uc = Ucur + so;
             S* Un = Unxt + so;
             S* dU = p.dU + so;
-            const long long sof = p.src_off[(long long)q * p.nsub + s];
+            const long long sof = r1.z;
+            const long long mo = q * p.mail_stride + r1.w;
             const C w = P::ld(p.wavelet + (long long)q * p.nsteps + n);
             cbar(nct);
             // padded copies of levels jl..j1 (local index = level - jl), one
@@ -479,10 +483,18 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
                 }
             }
             if constexpr (P::factored) {
-                // the increments of the updated levels, staged in sD
+                // the increments of the updated levels, staged in sD, and
+                // the source rows of levels jl..j1-1, staged in sSrc
                 for (int lj = ja - jl + warp; lj < nl; lj += ncw) {
                     const int j = jl + lj;
                     for (int i = lane; i < b; i += 32) cp_async<sizeof(S)>(sD + lj * bp + i, dU + j * b + i);
+                }
+                if (sof >= 0) {
+                    for (int lj = warp; lj < nl; lj += ncw) {
+                        const int j = jl + lj;
+                        for (int i = lane; i < b; i += 32)
+                            cp_async<sizeof(S)>(sSrc + lj * bp + i, p.src + sof + j * b + i);
+                    }
                 }
             }
             cp_async_wait_all();
@@ -494,7 +506,7 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
                 // the Gammahat_j owner forms psi_j = phi_j - phi_{j-1} + p_j f
                 // the same way and applies the increment update (Eq. 19) to
                 // its rows directly from the matvec.
-                const float* src = (sof >= 0) ? reinterpret_cast<const float*>(p.src) + sof : nullptr;
+                const bool has_src = sof >= 0;
                 const float wf = (float)w;
                 for (int half = 0; half < 2; ++half) {
                     const int lo = half ? ja : jl;
@@ -514,7 +526,7 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
                                          [&](int row) { return fU[bp + row] - fU[row]; },
                                          [&](int row, float v) { fP[row] = v; });
                         } else {
-                            const float* sj = src ? src + j * b : nullptr;
+                            const float* sj = reinterpret_cast<const float*>(sSrc) + (j - jl) * bp;
                             const float* fD = reinterpret_cast<const float*>(sD) + (j - jl) * bp;
                             float* dUj = reinterpret_cast<float*>(dU) + j * b;
                             float* Unj = reinterpret_cast<float*>(Un) + j * b;
@@ -522,7 +534,7 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
                             factor_apply_any(nt, tl,
                                          [&](int row) {
                                              float v = fP[row] - fP[row - bp];
-                                             if (sj && row < b) v += sj[row] * wf;
+                                             if (has_src && row < b) v += sj[row] * wf;
                                              return v;
                                          },
                                          [&](int row, float v) {
@@ -540,11 +552,9 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
                         cbar(nct);
                         // (2.1) publish face data [phi_1 + p_1 f]
                         if (j0 == 0) {
-                            S* my_mail = mail + q * p.mail_stride + p.mail_off[s];
-                            for (int i = threadIdx.x; i < b; i += nct) {
-                                const C srcv = (sof >= 0) ? P::mul(P::ld(p.src + sof + i), w) : P::zero();
-                                P::st(my_mail + i, P::add(sPhi[i], srcv));
-                            }
+                            S* my_mail = mail + mo;
+                            for (int i = threadIdx.x; i < b; i += nct)
+                                P::st(my_mail + i, has_src ? P::add(sPhi[i], P::mul(sSrc[i], w)) : sPhi[i]);
                         }
                     }
                 }
@@ -577,7 +587,7 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
                 if (half == 0) {
                     // (2.1) publish face data; psi_j for the updated levels
                     if (j0 == 0) {
-                        S* my_mail = mail + q * p.mail_stride + p.mail_off[s];
+                        S* my_mail = mail + mo;
                         for (int i = threadIdx.x; i < b; i += nct) {
                             const C srcv = (sof >= 0) ? P::mul(P::ld(p.src + sof + i), w) : P::zero();
                             P::st(my_mail + i, P::add(sPhi[i], srcv));
@@ -612,36 +622,31 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
 
         // ---------------- phase B: faces, Eq. (18) ----------------
         for (int pc = pc0; pc < pc1; ++pc) {
-            const int4 pe = p.pieces[pc];
-            if (pe.y != 0) continue;                     // faces belong to the level-0 piece
-            const int u = pe.x;
-            const int q = u / p.nsub, s = u - q * p.nsub;
-            const int b = p.sub_b[s];
-            const long long so = q * p.state_stride + p.state_off[s];
-            const S* mine = mail + q * p.mail_stride + p.mail_off[s];
-            const int* fo = p.face_off + s * 7;
+            const int4 r0 = p.prec[2 * pc];
+            if (r0.z != 0) continue;                     // faces belong to the level-0 piece
+            const int4 r1 = p.prec[2 * pc + 1];
+            const int q = r0.x, b = r1.x & 255;
+            const long long so = q * p.state_stride + r1.y;
+            const S* mailq = mail + q * p.mail_stride;
+            const int4* fr = p.frow + r1.w;
             cbar(nct);
             // sum of both sides' face data, lower subdomain index first
             for (int t = threadIdx.x; t < b; t += nct) {
-                int f = 0;
-                while (t >= fo[f + 1]) ++f;
-                const int nb = p.nbr[s * 6 + f];
-                C v = P::ld(mine + t);
-                if (nb >= 0) {
-                    const S* other = mail + q * p.mail_stride + p.mail_off[nb];
-                    const C o = P::ld(other + p.face_off[nb * 7 + (f ^ 1)] + (t - fo[f]));
-                    v = (nb < s) ? P::add(o, v) : P::add(v, o);
+                const int4 e = fr[t];
+                C v = P::ld(mailq + r1.w + t);
+                if (e.x >= 0) {
+                    const C o = P::ld(mailq + e.x);
+                    v = (e.z >> 16) ? P::add(o, v) : P::add(v, o);
                 }
                 sD[t] = v;
                 if (p.Kx) P::st(p.Kx + so + t, v);
             }
             cbar(nct);
             for (int t = threadIdx.x; t < b; t += nct) {
-                int f = 0;
-                while (t >= fo[f + 1]) ++f;
-                const int m = fo[f + 1] - fo[f], i = t - fo[f];
-                const S* H = p.H + p.H_off[s * 6 + f] + i;   // H symmetric
-                const C* v = sD + fo[f];
+                const int4 e = fr[t];
+                const int m = e.z & 0xffff;
+                const S* H = p.H + e.y;                  // row i of the symmetric H_f
+                const C* v = sD + e.w;
                 typename P::Acc acc = P::acc0();
                 for (int c = 0; c < m; ++c) P::fma(acc, P::ld(H + c * m), v[c]);
                 const C d = P::add(P::ld(p.dU + so + t), P::mul(dt2, P::get(acc)));
@@ -663,7 +668,7 @@ template <class P>
 size_t step_smem_bytes(int kmax, int bmax, int nstage) {
     const size_t bp = (size_t)((bmax + 7) / 8) * 8;
     size_t bytes = (size_t)nstage * sym_tiles(bmax) * 64 * sizeof(typename P::S);
-    bytes += sizeof(typename P::C) * ((size_t)(kmax + 1) * bp + 2 * (size_t)kmax * bp);
+    bytes += sizeof(typename P::C) * ((size_t)(kmax + 1) * bp + (P::factored ? 3 : 2) * (size_t)kmax * bp);
     bytes = (bytes + 15) & ~(size_t)15;
     return bytes + 2 * nstage * sizeof(unsigned long long);
 }
@@ -720,6 +725,62 @@ void build_pieces(int nunits, int nsub, const int* k_sub, int grid, std::vector<
         }
     }
     ptr[grid] = (int)pieces.size();
+}
+
+// Piece records, two int4 per piece: {shot, subdomain, j0, j1} and
+// {b | k << 8, state offset, source-row offset (with the shot, -1 if none),
+// face-data offset}.  False if an offset does not fit in 32 bits.
+bool piece_records(const std::vector<int4>& pieces, int nsub, const int* k, const int* b,
+                   const long long* state_off, const long long* src_off, const long long* mail_off,
+                   std::vector<int4>& rec) {
+    rec.resize(2 * pieces.size());
+    for (size_t i = 0; i < pieces.size(); ++i) {
+        const int u = pieces[i].x, q = u / nsub, s = u - q * nsub;
+        const long long sof = src_off[(size_t)q * nsub + s];
+        if (state_off[s] > INT_MAX || sof > INT_MAX || mail_off[s] > INT_MAX || b[s] > 255)
+            return false;
+        rec[2 * i] = make_int4(q, s, pieces[i].y, pieces[i].z);
+        rec[2 * i + 1] = make_int4(b[s] | (k[s] << 8), (int)state_off[s], (int)sof, (int)mail_off[s]);
+    }
+    return true;
+}
+
+// Per-row face table in the layout of the face data (row mail_off[s] + t):
+// {neighbour's face-data offset of the same face node (-1 on an outer face),
+//  offset of row i of H_f, m_f | (neighbour index < s) << 16, start of the
+//  face inside the b-vector}.
+bool face_rows(int nsub, const int* b, const int* face_off, const int* nbr,
+               const long long* H_off, const long long* mail_off, std::vector<int4>& rows) {
+    long long n = 0;
+    for (int s = 0; s < nsub; ++s) n += b[s];
+    rows.assign((size_t)n, make_int4(-1, 0, 0, 0));
+    for (int s = 0; s < nsub; ++s) {
+        for (int f = 0; f < 6; ++f) {
+            const int f0 = face_off[s * 7 + f], m = face_off[s * 7 + f + 1] - f0;
+            const int nb = nbr[s * 6 + f];
+            for (int i = 0; i < m; ++i) {
+                long long other = -1;
+                if (nb >= 0) other = mail_off[nb] + face_off[nb * 7 + (f ^ 1)] + i;
+                const long long h = H_off[s * 6 + f] + i;
+                if (other > INT_MAX || h > INT_MAX || mail_off[s] + f0 + i > INT_MAX) return false;
+                rows[(size_t)(mail_off[s] + f0 + i)] =
+                    make_int4((int)other, (int)h, m | ((nb >= 0 && nb < s) ? 1 << 16 : 0), f0);
+            }
+        }
+    }
+    return true;
+}
+
+// Receiver pair table: {k*b of its subdomain, row offset, state offset, 0}.
+bool readout_table(int nrpairs, const int* rp_sub, const long long* rp_off, const int* k,
+                   const int* b, const long long* state_off, std::vector<int4>& tab) {
+    tab.resize((size_t)std::max(nrpairs, 1), make_int4(0, 0, 0, 0));
+    for (int r = 0; r < nrpairs; ++r) {
+        const int s = rp_sub[r];
+        if (rp_off[r] > INT_MAX || state_off[s] > INT_MAX) return false;
+        tab[r] = make_int4(k[s] * b[s], (int)rp_off[r], (int)state_off[s], 0);
+    }
+    return true;
 }
 
 #define SFM_INST(P)                                                                             \
