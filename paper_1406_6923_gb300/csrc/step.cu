@@ -127,6 +127,15 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Bounded device-wide barrier among the consumer threads of every block.
 // Returns false (and sets *err) when it did not complete within timeout_ns
 // or another block reported an error; every block then leaves the kernel.
@@ -380,11 +389,16 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
     const int bpm = ((p.bmax + 7) / 8) * 8;
     const int stage_elems = (int)(sym_tiles(p.bmax) * 64);
     S* stages = reinterpret_cast<S*>(smem_raw);
-    C* sU = reinterpret_cast<C*>(stages + (size_t)nstage * stage_elems);   // (kmax+1)*bpm
-    C* sD = sU + (p.kmax + 1) * bpm;                     // kmax*bpm: Delta, then psi
-    C* sPhi = sD + p.kmax * bpm;                         // kmax*bpm: phi, then a
-    C* sSrc = sPhi + p.kmax * bpm;                       // kmax*bpm: source rows (factored)
-    C* sEnd = P::factored ? sSrc + p.kmax * bpm : sSrc;
+    // Per-piece staging: the factored path double-buffers the state,
+    // increment and source rows (set 1 at +SU / +SD) so the next piece loads
+    // while the current one computes.
+    constexpr int NSET = P::factored ? 2 : 1;
+    const int SU = (p.kmax + 1) * bpm, SD = p.kmax * bpm;
+    C* sU = reinterpret_cast<C*>(stages + (size_t)nstage * stage_elems);   // NSET x (kmax+1)*bpm
+    C* sD = sU + NSET * SU;                              // NSET x kmax*bpm: Delta/psi or increments
+    C* sPhi = sD + NSET * SD;                            // kmax*bpm: phi, then a; face sums
+    C* sSrc = sPhi + SD;                                 // NSET x kmax*bpm: source rows (factored)
+    C* sEnd = P::factored ? sSrc + NSET * SD : sSrc;
     unsigned long long* full = reinterpret_cast<unsigned long long*>(
         (reinterpret_cast<uintptr_t>(sEnd) + 15) & ~(uintptr_t)15);
     unsigned long long* empty = full + nstage;
@@ -452,6 +466,39 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
     int cst = 0, own = 0;
     unsigned cph = 0;
     bool dead = false;
+    // factored path: issue the copies of piece pcx into staging set `set`
+    // (one cp.async group per call; zero padding written directly)
+    auto stage = [&](int pcx, int set, const S* Ubuf) {
+        const int4 a0 = p.prec[2 * pcx], a1 = p.prec[2 * pcx + 1];
+        const int xj0 = a0.z, xj1 = a0.w, xb = a1.x & 255, xk = a1.x >> 8;
+        const int xbp = ((xb + 7) >> 3) * 8;
+        const int xjl = xj0 > 0 ? xj0 - 1 : 0, xja = xj0 > 1 ? xj0 : 1, xnl = xj1 - xjl;
+        const long long xso = a0.x * p.state_stride + a1.y, xsof = a1.z;
+        C* xU = sU + set * SU;
+        C* xD = sD + set * SD;
+        C* xS = sSrc + set * SD;
+        for (int lj = warp; lj <= xnl; lj += ncw) {
+            const int j = xjl + lj;
+            for (int i = lane; i < xbp; i += 32) {
+                if (j < xk && i < xb) cp_async<sizeof(S)>(xU + lj * xbp + i, Ubuf + xso + j * xb + i);
+                else xU[lj * xbp + i] = P::zero();
+            }
+        }
+        for (int lj = xja - xjl + warp; lj < xnl; lj += ncw) {
+            const int j = xjl + lj;
+            for (int i = lane; i < xb; i += 32)
+                cp_async<sizeof(S)>(xD + lj * xbp + i, p.dU + xso + j * xb + i);
+        }
+        if (xsof >= 0) {
+            for (int lj = warp; lj < xnl; lj += ncw) {
+                const int j = xjl + lj;
+                for (int i = lane; i < xb; i += 32)
+                    cp_async<sizeof(S)>(xS + lj * xbp + i, p.src + xsof + j * xb + i);
+            }
+        }
+        cp_async_commit();
+    };
+    bool pre = false;   // the first piece of this step was staged at the end of the last one
     for (int n = 0; n < p.nsteps; ++n) {
         const S* Ucur = p.U[n % 3];
         S* Unxt = p.U[(n + 1) % 3];
@@ -471,35 +518,21 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
             const long long sof = r1.z;
             const long long mo = q * p.mail_stride + r1.w;
             const C w = P::ld(p.wavelet + (long long)q * p.nsteps + n);
-            cbar(nct);
-            // padded copies of levels jl..j1 (local index = level - jl), one
-            // level per warp, lanes along the level
             static_assert(sizeof(C) == sizeof(S), "state copies are byte copies");
-            for (int lj = warp; lj <= nl; lj += ncw) {
-                const int j = jl + lj;
-                for (int i = lane; i < bp; i += 32) {
-                    if (j < k && i < b) cp_async<sizeof(S)>(sU + lj * bp + i, Uc + j * b + i);
-                    else sU[lj * bp + i] = P::zero();
-                }
-            }
             if constexpr (P::factored) {
-                // the increments of the updated levels, staged in sD, and
-                // the source rows of levels jl..j1-1, staged in sSrc
-                for (int lj = ja - jl + warp; lj < nl; lj += ncw) {
-                    const int j = jl + lj;
-                    for (int i = lane; i < b; i += 32) cp_async<sizeof(S)>(sD + lj * bp + i, dU + j * b + i);
+                const int set = (pc - pc0) & 1;
+                cbar(nct);
+                if (pc == pc0 && !pre) stage(pc, set, Ucur);
+                if (pc + 1 < pc1) {
+                    stage(pc + 1, set ^ 1, Ucur);
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
                 }
-                if (sof >= 0) {
-                    for (int lj = warp; lj < nl; lj += ncw) {
-                        const int j = jl + lj;
-                        for (int i = lane; i < b; i += 32)
-                            cp_async<sizeof(S)>(sSrc + lj * bp + i, p.src + sof + j * b + i);
-                    }
-                }
-            }
-            cp_async_wait_all();
-            cbar(nct);
-            if constexpr (P::factored) {
+                cbar(nct);
+                C* const sUs = sU + set * SU;
+                C* const sDs = sD + set * SD;
+                C* const sSs = sSrc + set * SD;
                 // One warp per streamed block (the owner of its stage).  The
                 // Gamma_j owner forms Delta_j = U_{j+1} - U_j as it loads it
                 // and leaves phi_j = L L^T Delta_j in sPhi; after the barrier
@@ -519,15 +552,15 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
                         if (!dead && !mbar_wait(full + st, ph, p.err, p.timeout_ns)) dead = true;
                         if (dead) continue;
                         const float* tl = reinterpret_cast<const float*>(stages) + (size_t)st * stage_elems;
-                        const float* fU = reinterpret_cast<const float*>(sU) + (j - jl) * bp;
+                        const float* fU = reinterpret_cast<const float*>(sUs) + (j - jl) * bp;
                         float* fP = reinterpret_cast<float*>(sPhi) + (j - jl) * bp;
                         if (half == 0) {
                             factor_apply_any(nt, tl,
                                          [&](int row) { return fU[bp + row] - fU[row]; },
                                          [&](int row, float v) { fP[row] = v; });
                         } else {
-                            const float* sj = reinterpret_cast<const float*>(sSrc) + (j - jl) * bp;
-                            const float* fD = reinterpret_cast<const float*>(sD) + (j - jl) * bp;
+                            const float* sj = reinterpret_cast<const float*>(sSs) + (j - jl) * bp;
+                            const float* fD = reinterpret_cast<const float*>(sDs) + (j - jl) * bp;
                             float* dUj = reinterpret_cast<float*>(dU) + j * b;
                             float* Unj = reinterpret_cast<float*>(Un) + j * b;
                             const float d2 = (float)dt2;
@@ -554,11 +587,23 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
                         if (j0 == 0) {
                             S* my_mail = mail + mo;
                             for (int i = threadIdx.x; i < b; i += nct)
-                                P::st(my_mail + i, has_src ? P::add(sPhi[i], P::mul(sSrc[i], w)) : sPhi[i]);
+                                P::st(my_mail + i, has_src ? P::add(sPhi[i], P::mul(sSs[i], w)) : sPhi[i]);
                         }
                     }
                 }
             } else {
+            cbar(nct);
+            // padded copies of levels jl..j1 (local index = level - jl), one
+            // level per warp, lanes along the level
+            for (int lj = warp; lj <= nl; lj += ncw) {
+                const int j = jl + lj;
+                for (int i = lane; i < bp; i += 32) {
+                    if (j < k && i < b) cp_async<sizeof(S)>(sU + lj * bp + i, Uc + j * b + i);
+                    else sU[lj * bp + i] = P::zero();
+                }
+            }
+            cp_async_wait_all();
+            cbar(nct);
             for (int t = threadIdx.x; t < nl * bp; t += nct) sD[t] = P::sub(sU[t + bp], sU[t]);
             cbar(nct);
             // phi_j = Gamma_j Delta_j for levels jl..j1-1, then after psi,
@@ -638,7 +683,7 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
                     const C o = P::ld(mailq + e.x);
                     v = (e.z >> 16) ? P::add(o, v) : P::add(v, o);
                 }
-                sD[t] = v;
+                sPhi[t] = v;
                 if (p.Kx) P::st(p.Kx + so + t, v);
             }
             cbar(nct);
@@ -646,12 +691,23 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
                 const int4 e = fr[t];
                 const int m = e.z & 0xffff;
                 const S* H = p.H + e.y;                  // row i of the symmetric H_f
-                const C* v = sD + e.w;
+                const C* v = sPhi + e.w;
                 typename P::Acc acc = P::acc0();
                 for (int c = 0; c < m; ++c) P::fma(acc, P::ld(H + c * m), v[c]);
                 const C d = P::add(P::ld(p.dU + so + t), P::mul(dt2, P::get(acc)));
                 P::st(p.dU + so + t, d);
                 P::st(Unxt + so + t, P::add(P::ld(Ucur + so + t), d));
+            }
+        }
+        pre = false;
+        if constexpr (P::factored) {
+            // stage the first piece of step n+1 (U^{n+1} is complete here for
+            // every piece of this block: interior levels before the barrier,
+            // this block's face levels just above) under the readout
+            if (n + 1 < p.nsteps && pc0 < pc1) {
+                cbar(nct);
+                stage(pc0, 0, Unxt);
+                pre = true;
             }
         }
         // receiver readout of U^n (complete since the barrier above)
@@ -668,7 +724,9 @@ template <class P>
 size_t step_smem_bytes(int kmax, int bmax, int nstage) {
     const size_t bp = (size_t)((bmax + 7) / 8) * 8;
     size_t bytes = (size_t)nstage * sym_tiles(bmax) * 64 * sizeof(typename P::S);
-    bytes += sizeof(typename P::C) * ((size_t)(kmax + 1) * bp + (P::factored ? 3 : 2) * (size_t)kmax * bp);
+    const size_t nset = P::factored ? 2 : 1;
+    bytes += sizeof(typename P::C) *
+             (nset * (size_t)(kmax + 1) * bp + (nset + 1 + (P::factored ? nset : 0)) * (size_t)kmax * bp);
     bytes = (bytes + 15) & ~(size_t)15;
     return bytes + 2 * nstage * sizeof(unsigned long long);
 }
