@@ -65,13 +65,14 @@ struct Cache {
 // Run buffers in one precision, grown on demand.
 template <typename T>
 struct RunBufs {
-    T *U[3] = {nullptr, nullptr, nullptr}, *dU = nullptr, *mail[2] = {nullptr, nullptr};
+    T *U[4] = {nullptr, nullptr, nullptr, nullptr}, *dU = nullptr, *mail[2] = {nullptr, nullptr};
     T *wavelet = nullptr, *partial = nullptr;
-    size_t n_state = 0, n_mail = 0, n_wav = 0, n_part = 0;
+    unsigned* rctr = nullptr;
+    size_t n_state = 0, n_mail = 0, n_wav = 0, n_part = 0, n_ctr = 0;
     void release() {
         for (auto& u : U) dfree(u);
-        dfree(dU); dfree(mail[0]); dfree(mail[1]); dfree(wavelet); dfree(partial);
-        n_state = n_mail = n_wav = n_part = 0;
+        dfree(dU); dfree(mail[0]); dfree(mail[1]); dfree(wavelet); dfree(partial); dfree(rctr);
+        n_state = n_mail = n_wav = n_part = n_ctr = 0;
     }
 };
 
@@ -556,13 +557,14 @@ static int run_impl(sfm_handle* h, double dt, int nsteps, const double* wavelet,
     const size_t npart = (size_t)h->nshots * (nsteps + 1) * h->nrpairs;
     const size_t ntr = (size_t)h->nshots * h->nrec * (nsteps + 1);
     size_t have_state = r.n_state;
-    for (int i = 0; i < 3; ++i) { size_t hs = have_state; CK(h, grow(r.U[i], hs, nst)); }
+    for (int i = 0; i < 4; ++i) { size_t hs = have_state; CK(h, grow(r.U[i], hs, nst)); }
     { size_t hs = have_state; CK(h, grow(r.dU, hs, nst)); r.n_state = hs; }
     size_t have_mail = r.n_mail;
     { size_t hm = have_mail; CK(h, grow(r.mail[0], hm, nml)); }
     { size_t hm = have_mail; CK(h, grow(r.mail[1], hm, nml)); r.n_mail = hm; }
     CK(h, grow(r.wavelet, r.n_wav, nwav));
     CK(h, grow(r.partial, r.n_part, npart));
+    CK(h, grow(r.rctr, r.n_ctr, (size_t)nsteps + 1));
     double* d_traces = traces;
     if (!(flags & SFM_DEVICE_PTR)) {
         CK(h, grow(x->d_traces, x->n_traces, ntr));
@@ -579,7 +581,8 @@ static int run_impl(sfm_handle* h, double dt, int nsteps, const double* wavelet,
     int launches = 0;
     CK(h, sfm::launch_convert<P>(d_wav64, r.wavelet, nwav, st));
     ++launches;
-    for (int i = 0; i < 3; ++i) CK(h, cudaMemsetAsync(r.U[i], 0, nst * sizeof(T), st));
+    for (int i = 0; i < 4; ++i) CK(h, cudaMemsetAsync(r.U[i], 0, nst * sizeof(T), st));
+    CK(h, cudaMemsetAsync(r.rctr, 0, ((size_t)nsteps + 1) * sizeof(unsigned), st));
     CK(h, cudaMemsetAsync(r.dU, 0, nst * sizeof(T), st));
     CK(h, cudaMemsetAsync(h->d_bar, 0, sizeof(unsigned int), st));
     CK(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
@@ -591,7 +594,8 @@ static int run_impl(sfm_handle* h, double dt, int nsteps, const double* wavelet,
     p.sub_b = h->d_b; p.sub_k = h->d_k; p.coef_off = h->d_tcoef_off; p.coef = c.coef;
     p.face_off = h->d_face_off; p.nbr = h->d_nbr; p.H_off = h->d_H_off; p.H = c.H;
     p.state_off = h->d_state_off; p.state_stride = h->nstate;
-    for (int i = 0; i < 3; ++i) p.U[i] = r.U[i];
+    for (int i = 0; i < 4; ++i) p.U[i] = r.U[i];
+    p.rctr = r.rctr;
     p.dU = r.dU;
     p.mail_off = h->d_mail_off; p.mail_stride = h->nmail; p.mail0 = r.mail[0]; p.mail1 = r.mail[1];
     p.src_off = h->d_src_off; p.src = c.src; p.wavelet = r.wavelet;
@@ -800,6 +804,8 @@ extern "C" int sfm_cfl_dt(sfm_handle* h, int iters, double* lambda_max, double* 
     p.face_off = h->d_face_off; p.nbr = h->d_nbr; p.H_off = h->d_H_off; p.H = c.H;
     p.state_off = h->d_state_off; p.state_stride = h->nstate;
     for (int i = 0; i < 3; ++i) p.U[i] = U[i];
+    p.U[3] = nullptr;                                // one step: U[0] -> U[1]
+    p.rctr = nullptr;                                // no receivers
     p.dU = dU;
     p.mail_off = h->d_mail_off; p.mail_stride = h->nmail; p.mail0 = mail0; p.mail1 = mail1;
     p.src_off = soff; p.src = c.src; p.wavelet = wav;

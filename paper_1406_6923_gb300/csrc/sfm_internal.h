@@ -31,7 +31,7 @@ struct StepParams {
     const T* H;
     const long long* state_off;  // [nsub] offset of the k*b state of shot 0
     long long state_stride;      // per shot
-    T* U[3];                     // state buffers, U^n lives in U[n % 3]
+    T* U[4];                     // state buffers, U^n lives in U[n % 4]
     T* dU;                       // increments (one buffer, updated in place)
     const long long* mail_off;   // [nsub] offset of the b-vector of shot 0
     long long mail_stride;       // per shot
@@ -45,6 +45,7 @@ struct StepParams {
     const long long* rp_off;     // [nrpairs] offset of its (k*b) row
     const T* rrows;
     T* partial;                  // [nshots][nsteps+1][nrpairs]
+    unsigned* rctr;              // [nsteps+1] readout item counters, zero at launch
     double dt2;
     unsigned int* bar;           // grid barrier counter (zeroed before launch)
     int* err;                    // device error word (0 = ok)

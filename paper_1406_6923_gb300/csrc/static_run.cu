@@ -157,12 +157,13 @@ extern "C" int sfm_run_static(int device, void* stream, int nsub, const int* k_s
                  o_rs = cv.take<int>(nrec_pairs), o_ro = cv.take<long long>(nrec_pairs),
                  o_rp = cv.take<int>(nrec + 1), o_pr = cv.take<int>(nrec_pairs);
     const size_t o_tiles = cv.take<double>((size_t)to), o_H = cv.take<double>((size_t)ho);
-    size_t o_U[3];
+    size_t o_U[4];
     for (auto& u : o_U) u = cv.take<double>((size_t)nshots * so);
     const size_t o_dU = cv.take<double>((size_t)nshots * so), o_m0 = cv.take<double>((size_t)nshots * mo),
                  o_m1 = cv.take<double>((size_t)nshots * mo),
                  o_part = cv.take<double>((size_t)nshots * (nsteps + 1) * std::max(nrec_pairs, 1)),
-                 o_bar = cv.take<unsigned int>(1), o_err = cv.take<int>(1), o_bad = cv.take<int>(1);
+                 o_bar = cv.take<unsigned int>(1), o_err = cv.take<int>(1), o_bad = cv.take<int>(1),
+                 o_ctr = cv.take<unsigned int>((size_t)nsteps + 1);
     if (cv.off > SFM_STATIC_SCRATCH_BYTES)
         return sfail(SFM_ERR_ARG, "sfm_run_static: problem needs " + std::to_string(cv.off) +
                                       " bytes of scratch, the static limit is " +
@@ -207,6 +208,7 @@ extern "C" int sfm_run_static(int device, void* stream, int nsub, const int* k_s
     SCK(cudaMemsetAsync(at(o_dU), 0, (size_t)nshots * so * sizeof(double), st));
     SCK(cudaMemsetAsync(at(o_part), 0, (size_t)nshots * (nsteps + 1) * std::max(nrec_pairs, 1) * sizeof(double), st));
     SCK(cudaMemsetAsync(at(o_bar), 0, sizeof(unsigned int), st));
+    SCK(cudaMemsetAsync(at(o_ctr), 0, ((size_t)nsteps + 1) * sizeof(unsigned int), st));
     SCK(cudaMemsetAsync(at(o_err), 0, sizeof(int), st));
     SCK(cudaMemsetAsync(at(o_bad), 0, sizeof(int), st));
     // face coupling blocks and the tile-packed coefficient copy
@@ -223,7 +225,8 @@ extern "C" int sfm_run_static(int device, void* stream, int nsub, const int* k_s
     p.face_off = (const int*)at(o_fo); p.nbr = (const int*)at(o_nb);
     p.H_off = (const long long*)at(o_ho); p.H = (const double*)at(o_H);
     p.state_off = (const long long*)at(o_so); p.state_stride = so;
-    for (int i = 0; i < 3; ++i) p.U[i] = (double*)at(o_U[i]);
+    for (int i = 0; i < 4; ++i) p.U[i] = (double*)at(o_U[i]);
+    p.rctr = (unsigned*)at(o_ctr);
     p.dU = (double*)at(o_dU);
     p.mail_off = (const long long*)at(o_mo); p.mail_stride = mo;
     p.mail0 = (double*)at(o_m0); p.mail1 = (double*)at(o_m1);

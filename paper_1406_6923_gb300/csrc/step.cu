@@ -13,15 +13,16 @@
 //   phase B (per unit, reads the neighbours' mail):
 //     a_f = H_f (mail_f(self) + mail_f(neighbour))  (outer face: own term)  (Eq. 18)
 //     delta_1,f += dt^2 a_f,  U_1,f^{n+1} = U_1,f^n + delta_1,f
-//     plus this block's share of the receiver readout of U^n
+//   the receiver readout of U^n runs inside the next step's barrier, between
+//   this block's arrival and its wait, taken item by item from a counter
 //
 // Each subdomain keeps its own copy of its level-1 face blocks; both sides
 // of a shared face compute the same sum of the same two mail vectors with
 // the same H_f copy, so the two copies stay bitwise equal (the continuity
-// condition of Eq. 17).  U^n lives in buffer n % 3 and the mail in buffer
+// condition of Eq. 17).  U^n lives in buffer n % 4 and the mail in buffer
 // n % 2: a block that runs ahead into phase A of step n+1 then never writes
-// what a slower block still reads in phase B of step n, so one barrier per
-// step suffices.
+// what a slower block still reads in phase B of step n or in the readout,
+// so one barrier per step suffices.
 #include "sfm_internal.h"
 
 #include <cooperative_groups.h>
@@ -136,16 +137,24 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Bounded device-wide barrier among the consumer threads of every block.
-// Returns false (and sets *err) when it did not complete within timeout_ns
-// or another block reported an error; every block then leaves the kernel.
-__device__ bool grid_barrier(unsigned int* bar, unsigned int target, int* err,
-                             unsigned long long timeout_ns, int skip_arrive, int nct) {
-    __shared__ int s_ok;
+// Bounded device-wide barrier among the consumer threads of every block, in
+// two halves: grid_arrive publishes the block's writes and counts it in;
+// grid_wait returns once every block has arrived, or false (with *err set)
+// when that did not happen within timeout_ns or another block reported an
+// error; every block then leaves the kernel.  Work that reads only data
+// finished before the previous barrier may run between the two halves.
+__device__ __forceinline__ void grid_arrive(unsigned int* bar, int skip_arrive, int nct) {
     cbar(nct);
     if (threadIdx.x == 0) {
         __threadfence();
         if ((int)blockIdx.x != skip_arrive) red_release_add_u32(bar, 1u);
+    }
+}
+
+__device__ bool grid_wait(unsigned int* bar, unsigned int target, int* err,
+                          unsigned long long timeout_ns, int nct) {
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
         int ok = 1;
         unsigned long long t0 = global_ns();
         while (ld_acquire_u32(bar) < target) {
@@ -163,6 +172,12 @@ __device__ bool grid_barrier(unsigned int* bar, unsigned int target, int* err,
     return s_ok != 0;
 }
 
+__device__ bool grid_barrier(unsigned int* bar, unsigned int target, int* err,
+                             unsigned long long timeout_ns, int skip_arrive, int nct) {
+    grid_arrive(bar, skip_arrive, nct);
+    return grid_wait(bar, target, err, timeout_ns, nct);
+}
+
 template <typename T>
 __device__ __forceinline__ T block_sum(T v, T* red) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -178,16 +193,24 @@ __device__ __forceinline__ T block_sum(T v, T* red) {
 }
 
 // Receiver readout of U (buffer `Ubuf`) at sample n.  Every (shot, pair)
-// item is one warp's compensated dot product of the pair's row with the
-// subdomain's state; items are spread over all consumer warps of the grid.
+// item is one warp's dot product (policy arithmetic) of the pair's row with
+// the subdomain's state.  Warps take items two at a time from the sample's
+// counter p.rctr[n] (zero at launch), so blocks with idle time take more.
 template <class P>
 __device__ void readout(const StepParams<typename P::S>& p, const typename P::S* Ubuf, int n) {
     using C = typename P::C;
-    const long long items = (long long)p.nshots * p.nrpairs;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (long long it = (long long)blockIdx.x * p.ncw + warp; it < items;
-         it += (long long)gridDim.x * p.ncw) {
-        const int q = (int)(it / p.nrpairs), r = (int)(it - (long long)q * p.nrpairs);
+    const int items = p.nshots * p.nrpairs;
+    if (items == 0) return;
+    const int lane = threadIdx.x & 31;
+    constexpr int CHUNK = 2;
+    for (;;) {
+        int base = 0;
+        if (lane == 0) base = (int)atomicAdd(p.rctr + n, (unsigned)CHUNK);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= items) break;
+        const int iend = base + CHUNK < items ? base + CHUNK : items;
+    for (int it = base; it < iend; ++it) {
+        const int q = it / p.nrpairs, r = it - q * p.nrpairs;
         const int4 e = p.rtab[r];
         const int kb = e.x;
         const typename P::S* row = p.rrows + e.y;
@@ -203,6 +226,7 @@ __device__ void readout(const StepParams<typename P::S>& p, const typename P::S*
         C v = P::get(P::merge(a0, a1));
         for (int o = 16; o > 0; o >>= 1) v = P::add(v, P::shfl_xor(v, o));
         if (lane == 0) P::st(p.partial + ((long long)q * (p.nsteps + 1) + n) * p.nrpairs + r, v);
+    }
     }
 }
 
@@ -404,6 +428,14 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
     unsigned long long* empty = full + nstage;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int pc0 = p.piece_ptr[blockIdx.x], pc1 = p.piece_ptr[blockIdx.x + 1];
+    // the block's first piece records, cached in shared memory
+    constexpr int REC_CACHE = 8;
+    __shared__ int4 s_rec[2 * REC_CACHE];
+    for (int t = threadIdx.x; t < 2 * min(pc1 - pc0, REC_CACHE); t += blockDim.x)
+        s_rec[t] = p.prec[2 * pc0 + t];
+    auto prec = [&](int pc, int half) -> int4 {
+        return (pc - pc0 < REC_CACHE) ? s_rec[2 * (pc - pc0) + half] : p.prec[2 * pc + half];
+    };
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < nstage; ++i) {
@@ -423,7 +455,7 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
         bool ok = true;
         for (int n = 0; n < p.nsteps && ok; ++n) {
             for (int pc = pc0; pc < pc1 && ok; ++pc) {
-                const int4 r0 = p.prec[2 * pc], r1 = p.prec[2 * pc + 1];
+                const int4 r0 = prec(pc, 0), r1 = prec(pc, 1);
                 const int s = r0.y, j0 = r0.z, j1 = r0.w;
                 const int b = r1.x & 255;
                 const int nt = (b + 7) >> 3;
@@ -469,7 +501,7 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
     // factored path: issue the copies of piece pcx into staging set `set`
     // (one cp.async group per call; zero padding written directly)
     auto stage = [&](int pcx, int set, const S* Ubuf) {
-        const int4 a0 = p.prec[2 * pcx], a1 = p.prec[2 * pcx + 1];
+        const int4 a0 = prec(pcx, 0), a1 = prec(pcx, 1);
         const int xj0 = a0.z, xj1 = a0.w, xb = a1.x & 255, xk = a1.x >> 8;
         const int xbp = ((xb + 7) >> 3) * 8;
         const int xjl = xj0 > 0 ? xj0 - 1 : 0, xja = xj0 > 1 ? xj0 : 1, xnl = xj1 - xjl;
@@ -500,13 +532,13 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
     };
     bool pre = false;   // the first piece of this step was staged at the end of the last one
     for (int n = 0; n < p.nsteps; ++n) {
-        const S* Ucur = p.U[n % 3];
-        S* Unxt = p.U[(n + 1) % 3];
+        const S* Ucur = p.U[n & 3];
+        S* Unxt = p.U[(n + 1) & 3];
         S* mail = (n & 1) ? p.mail1 : p.mail0;
 
         // ---------------- phase A ----------------
         for (int pc = pc0; pc < pc1; ++pc) {
-            const int4 r0 = p.prec[2 * pc], r1 = p.prec[2 * pc + 1];
+            const int4 r0 = prec(pc, 0), r1 = prec(pc, 1);
             const int q = r0.x, j0 = r0.z, j1 = r0.w;
             const int b = r1.x & 255, k = r1.x >> 8;
             const int nt = (b + 7) >> 3, bp = nt * 8;
@@ -661,15 +693,20 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
             }
         }
 
-        if (!grid_barrier(p.bar, (unsigned)(n + 1) * gridDim.x, p.err, p.timeout_ns,
-                          p.skip_arrive, nct))
+        // Arrive, then read out U^{n-1} (buffer (n-1) & 3, complete before
+        // the previous barrier and rewritten only by phase A of step n+2,
+        // after the next barrier, which needs this block) while the slower
+        // blocks finish phase A, then wait.
+        grid_arrive(p.bar, p.skip_arrive, nct);
+        if (n > 0) readout<P>(p, p.U[(n - 1) & 3], n - 1);
+        if (!grid_wait(p.bar, (unsigned)(n + 1) * gridDim.x, p.err, p.timeout_ns, nct))
             return;
 
         // ---------------- phase B: faces, Eq. (18) ----------------
         for (int pc = pc0; pc < pc1; ++pc) {
-            const int4 r0 = p.prec[2 * pc];
+            const int4 r0 = prec(pc, 0);
             if (r0.z != 0) continue;                     // faces belong to the level-0 piece
-            const int4 r1 = p.prec[2 * pc + 1];
+            const int4 r1 = prec(pc, 1);
             const int q = r0.x, b = r1.x & 255;
             const long long so = q * p.state_stride + r1.y;
             const S* mailq = mail + q * p.mail_stride;
@@ -701,23 +738,22 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
         }
         pre = false;
         if constexpr (P::factored) {
-            // stage the first piece of step n+1 (U^{n+1} is complete here for
-            // every piece of this block: interior levels before the barrier,
-            // this block's face levels just above) under the readout
+            // stage the first piece of step n+1 now: U^{n+1} is complete for
+            // every piece of this block (interior levels before the barrier,
+            // this block's face levels just above)
             if (n + 1 < p.nsteps && pc0 < pc1) {
                 cbar(nct);
                 stage(pc0, 0, Unxt);
                 pre = true;
             }
         }
-        // receiver readout of U^n (complete since the barrier above)
-        readout<P>(p, Ucur, n);
     }
-    // final readout of U^{nsteps}, after every face update of the last step
-    if (!grid_barrier(p.bar, (unsigned)(p.nsteps + 1) * gridDim.x, p.err, p.timeout_ns,
-                      p.skip_arrive, nct))
+    // the last two samples, after every face update of the last step
+    grid_arrive(p.bar, p.skip_arrive, nct);
+    readout<P>(p, p.U[(p.nsteps - 1) & 3], p.nsteps - 1);
+    if (!grid_wait(p.bar, (unsigned)(p.nsteps + 1) * gridDim.x, p.err, p.timeout_ns, nct))
         return;
-    readout<P>(p, p.U[p.nsteps % 3], p.nsteps);
+    readout<P>(p, p.U[p.nsteps & 3], p.nsteps);
 }
 
 template <class P>
