@@ -209,24 +209,48 @@ __device__ void readout(const StepParams<typename P::S>& p, const typename P::S*
         base = __shfl_sync(0xffffffffu, base, 0);
         if (base >= items) break;
         const int iend = base + CHUNK < items ? base + CHUNK : items;
-    for (int it = base; it < iend; ++it) {
-        const int q = it / p.nrpairs, r = it - q * p.nrpairs;
-        const int4 e = p.rtab[r];
-        const int kb = e.x;
-        const typename P::S* row = p.rrows + e.y;
-        const typename P::S* U = Ubuf + q * p.state_stride + e.z;
-        typename P::Acc a0 = P::acc0(), a1 = P::acc0();
-        int t = lane;
-#pragma unroll 4
-        for (; t + 32 < kb; t += 64) {
-            P::fma(a0, P::ld(row + t), P::ld(U + t));
-            P::fma(a1, P::ld(row + t + 32), P::ld(U + t + 32));
+        for (int it = base; it < iend; ++it) {
+            const int q = it / p.nrpairs, r = it - q * p.nrpairs;
+            const int4 e = p.rtab[r];
+            const int kb = e.x;
+            const typename P::S* row = p.rrows + e.y;
+            const typename P::S* U = Ubuf + q * p.state_stride + e.z;
+            C v;
+            if constexpr (sizeof(typename P::S) == 4) {
+                // FP32 rows and state: 16-byte loads, all of a lane's loads in
+                // flight at once when k*b is a multiple of 4 and both are aligned
+                if ((kb & 3) == 0 && ((reinterpret_cast<uintptr_t>(row) | reinterpret_cast<uintptr_t>(U)) & 15) == 0) {
+                    const float4* r4 = reinterpret_cast<const float4*>(row);
+                    const float4* u4 = reinterpret_cast<const float4*>(U);
+                    float a0 = 0.f, a1 = 0.f;
+    #pragma unroll 8
+                    for (int t = lane; t < (kb >> 2); t += 32) {
+                        const float4 x = r4[t], y = u4[t];
+                        a0 = fmaf(x.x, y.x, a0);
+                        a1 = fmaf(x.y, y.y, a1);
+                        a0 = fmaf(x.z, y.z, a0);
+                        a1 = fmaf(x.w, y.w, a1);
+                    }
+                    v = a0 + a1;
+                } else {
+                    float a0 = 0.f;
+                    for (int t = lane; t < kb; t += 32) a0 = fmaf(row[t], U[t], a0);
+                    v = a0;
+                }
+            } else {
+                typename P::Acc a0 = P::acc0(), a1 = P::acc0();
+                int t = lane;
+    #pragma unroll 4
+                for (; t + 32 < kb; t += 64) {
+                    P::fma(a0, P::ld(row + t), P::ld(U + t));
+                    P::fma(a1, P::ld(row + t + 32), P::ld(U + t + 32));
+                }
+                if (t < kb) P::fma(a0, P::ld(row + t), P::ld(U + t));
+                v = P::get(P::merge(a0, a1));
+            }
+            for (int o = 16; o > 0; o >>= 1) v = P::add(v, P::shfl_xor(v, o));
+            if (lane == 0) P::st(p.partial + ((long long)q * (p.nsteps + 1) + n) * p.nrpairs + r, v);
         }
-        if (t < kb) P::fma(a0, P::ld(row + t), P::ld(U + t));
-        C v = P::get(P::merge(a0, a1));
-        for (int o = 16; o > 0; o >>= 1) v = P::add(v, P::shfl_xor(v, o));
-        if (lane == 0) P::st(p.partial + ((long long)q * (p.nsteps + 1) + n) * p.nrpairs + r, v);
-    }
     }
 }
 
@@ -792,33 +816,64 @@ cudaError_t launch_step(const StepParams<typename P::S>& p, int grid, cudaStream
 }
 
 // Pieces of work per block: the (unit, level) sequence, unit-major, cut into
-// `grid` contiguous ranges of (nearly) equal length.  A unit is never cut at
-// level 1: a piece starting there would read the level-0 face blocks, which
-// the level-0 piece updates after the device-wide barrier, with no barrier
-// before the next step's phase A; pieces starting at level >= 2 read only
-// interior levels, which are written before the barrier.
+// contiguous pieces, one list per block, so that the blocks' estimated costs
+// are as even as a greedy fill allows.  Cost unit: one level (its two block
+// products); a block's second and later pieces add their staging and
+// barriers, a level-0 piece adds the face data and the face update, and a
+// piece starting at level >= 2 recomputes phi_{j0-1}.  The smallest
+// capacity whose greedy fill needs at most `grid` blocks is found by
+// bisection.  A unit is never cut at level 1: a piece starting there would
+// read the level-0 face blocks, which the level-0 piece updates after the
+// device-wide barrier, with no barrier before the next step's phase A;
+// pieces starting at level >= 2 read only interior levels, which are
+// written before the barrier.
 void build_pieces(int nunits, int nsub, const int* k_sub, int grid, std::vector<int>& ptr,
                   std::vector<int4>& pieces) {
+    const double kPiece = 2.0, kFace = 2.0, kLead = 0.5;
     long long total = 0;
-    for (int u = 0; u < nunits; ++u) total += k_sub[u % nsub];
-    ptr.assign(grid + 1, 0);
-    pieces.clear();
-    int u = 0, j = 0;
-    long long pos = 0;
-    for (int c = 0; c < grid; ++c) {
-        const long long end = total * (c + 1) / grid;
-        ptr[c] = (int)pieces.size();
-        while (pos < end && u < nunits) {
-            const int k = k_sub[u % nsub];
-            int take = (int)std::min<long long>(end - pos, k - j);
-            if (j + take == 1 && k > 1) take = 2 - j;   // no cut at level 1
-            pieces.push_back(make_int4(u, j, j + take, 0));
-            j += take;
-            pos += take;
-            if (j == k) { ++u; j = 0; }
-        }
+    int kmax = 1;
+    for (int u = 0; u < nunits; ++u) {
+        total += k_sub[u % nsub];
+        kmax = std::max(kmax, k_sub[u % nsub]);
     }
-    ptr[grid] = (int)pieces.size();
+    auto fill = [&](double cap, bool emit) -> int {
+        if (emit) { ptr.assign(grid + 1, 0); pieces.clear(); }
+        int blocks = 0, u = 0, j = 0;
+        while (u < nunits) {
+            if (emit) {
+                if (blocks >= grid) return blocks + 1;
+                ptr[blocks] = (int)pieces.size();
+            }
+            ++blocks;
+            double used = 0.0;
+            int np = 0;
+            while (u < nunits) {
+                const int k = k_sub[u % nsub];
+                const double over = (np > 0 ? kPiece : 0.0) + (j == 0 ? kFace : 0.0) + (j >= 2 ? kLead : 0.0);
+                int take = (int)std::min<double>(k - j, std::floor(cap - used - over));
+                if (j + take == 1 && k > 1) take = (cap - used - over >= 2.0) ? 2 : 0;   // no cut at level 1
+                if (take <= 0 && np == 0) take = (j == 0 && k > 1) ? 2 : 1;             // always progress
+                if (take <= 0) break;
+                if (emit) pieces.push_back(make_int4(u, j, j + take, 0));
+                used += over + take;
+                ++np;
+                j += take;
+                const bool whole = (j == k);
+                if (whole) { ++u; j = 0; }
+                if (!whole) break;                                                     // block full
+            }
+        }
+        if (emit)
+            for (int c = blocks; c <= grid; ++c) ptr[c] = (int)pieces.size();
+        return blocks;
+    };
+    double lo = (double)total / grid, hi = lo + kmax + 4 * (kPiece + kFace + kLead) + 2;
+    while (fill(hi, false) > grid) hi *= 2;
+    for (int it = 0; it < 40 && hi - lo > 1e-3; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (fill(mid, false) <= grid) hi = mid; else lo = mid;
+    }
+    fill(hi, true);
 }
 
 // Piece records, two int4 per piece: {shot, subdomain, j0, j1} and
