@@ -526,6 +526,12 @@ static int step_setup(sfm_handle* h, int nunits, const long long* src_off,
     }
     p.ncw = ncw;
     p.nstage = nstage;
+    p.stage_v4 = 0;
+    if (P::factored) {
+        p.stage_v4 = 1;
+        for (int s = 0; s < h->nsub; ++s)
+            if (h->b[s] % 4 != 0) p.stage_v4 = 0;
+    }
     p.piece_ptr = x->d_piece_ptr;
     p.prec = x->d_prec;
     p.frow = h->d_frow;

@@ -58,6 +58,8 @@ struct StepParams {
     const int4* prec;            // [2*npieces] piece records (see piece_records)
     const int4* frow;            // [mail layout] face rows (see face_rows)
     const int4* rtab;            // [nrpairs] receiver pairs (see readout_table)
+    int stage_v4;                // factored path: stage piece state with 16-byte copies
+                                 // (every b a multiple of 4, FP32 storage)
 };
 
 // launchers (step.cu); P is a number policy of numeric.cuh

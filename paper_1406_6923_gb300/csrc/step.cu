@@ -533,6 +533,31 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
         C* xU = sU + set * SU;
         C* xD = sD + set * SD;
         C* xS = sSrc + set * SD;
+        if (p.stage_v4) {
+            // every width a multiple of 4: 16-byte copies, zero padding from
+            // b to the tile width and for level k (if reached)
+            for (int lj = warp; lj <= xnl; lj += ncw) {
+                const int j = xjl + lj;
+                for (int i = 4 * lane; i < xbp; i += 128) {
+                    if (j < xk && i < xb) cp_async<16>(xU + lj * xbp + i, Ubuf + xso + j * xb + i);
+                    else *reinterpret_cast<float4*>(xU + lj * xbp + i) = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+            for (int lj = xja - xjl + warp; lj < xnl; lj += ncw) {
+                const int j = xjl + lj;
+                for (int i = 4 * lane; i < xb; i += 128)
+                    cp_async<16>(xD + lj * xbp + i, p.dU + xso + j * xb + i);
+            }
+            if (xsof >= 0) {
+                for (int lj = warp; lj < xnl; lj += ncw) {
+                    const int j = xjl + lj;
+                    for (int i = 4 * lane; i < xb; i += 128)
+                        cp_async<16>(xS + lj * xbp + i, p.src + xsof + j * xb + i);
+                }
+            }
+            cp_async_commit();
+            return;
+        }
         for (int lj = warp; lj <= xnl; lj += ncw) {
             const int j = xjl + lj;
             for (int i = lane; i < xbp; i += 32) {
@@ -579,8 +604,8 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
                 const int set = (pc - pc0) & 1;
                 cbar(nct);
                 if (pc == pc0 && !pre) stage(pc, set, Ucur);
+                if (pc + 1 < pc1) stage(pc + 1, set ^ 1, Ucur);
                 if (pc + 1 < pc1) {
-                    stage(pc + 1, set ^ 1, Ucur);
                     cp_async_wait<1>();
                 } else {
                     cp_async_wait<0>();
