@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--nsteps", type=int, default=None, help="time steps per run (default: 4000)")
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32f", "fp32", "fp32x2", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-steps", type=int, default=60)
+    ap.add_argument("--cpu-sample-steps", type=int, default=600)
     ap.add_argument("--shape", default=None,
                     help="fixed stepping block shape 'warps,stages' instead of the autotuner's")
     return ap.parse_args()
