@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32f", "fp32", "fp32x2", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=600)
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3"],
+                    help="cfg2: 192^3 cells, 512 subdomains, 1 shot (the headline); "
+                         "cfg3: 256x256x128 cells, uneven subdomains, 64 shots")
     ap.add_argument("--shape", default=None,
                     help="fixed stepping block shape 'warps,stages' instead of the autotuner's")
     return ap.parse_args()
@@ -142,17 +145,38 @@ def peaks():
         return {"hbm_gbs": FALLBACK_HBM}, "fallback"
 
 
-def algorithmic_bytes_per_step(nsub, b, k, m, nrpairs, word):
-    """Bytes one time step must move for one shot (the per-unit figure of the
-    roofline): packed symmetric Gamma_1..k and Gammahat_2..k, U and delta read
-    and written, the face blocks H_f, the face data written and read back,
-    and the receiver rows; ``word`` bytes per number."""
-    coef = nsub * (2 * k - 1) * b * (b + 1) // 2
-    state = nsub * 4 * k * b
-    faces = nsub * 6 * m * (m + 1) // 2
-    mail = nsub * 2 * b
-    rec = nrpairs * k * b
-    return (coef + state + faces + mail + rec) * word
+def face_modes(p):
+    """Modes per (subdomain, face) of a problem: a shared face carries the
+    smaller of its two subdomains' m, an outer face its own (the layout rule
+    of the face basis); faces ordered -x, +x, -y, +y, -z, +z."""
+    ncx, ncy, ncz = len(p.xcuts) - 1, len(p.ycuts) - 1, len(p.zcuts) - 1
+    m = np.asarray(p.m_sub).reshape(ncz, ncy, ncx)
+    out = np.zeros((p.nsub, 6), dtype=int)
+    for iz in range(ncz):
+        for iy in range(ncy):
+            for ix in range(ncx):
+                s = ix + ncx * (iy + ncy * iz)
+                for f, (dx, dy, dz) in enumerate(((-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0),
+                                                  (0, 0, -1), (0, 0, 1))):
+                    jx, jy, jz = ix + dx, iy + dy, iz + dz
+                    inside = 0 <= jx < ncx and 0 <= jy < ncy and 0 <= jz < ncz
+                    out[s, f] = min(m[iz, iy, ix], m[jz, jy, jx]) if inside else m[iz, iy, ix]
+    return out
+
+
+def algorithmic_bytes_per_step(p, nshots, receiver_numbers, word):
+    """Bytes one time step must move (the roofline's per-step figure): once
+    per step the coefficient blocks (Gamma_1..k and Gammahat_2..k, each
+    b(b+1)/2 numbers, packed symmetric or triangular factor), the face blocks
+    H_f and the receiver rows (``receiver_numbers`` in all); per shot U and
+    delta read and written and the face data written and read back; ``word``
+    bytes per number."""
+    mf = face_modes(p)
+    b = mf.sum(axis=1)
+    k = np.asarray(p.k_sub)
+    coef = int(((2 * k - 1) * b * (b + 1) // 2).sum() + (mf * (mf + 1) // 2).sum() + receiver_numbers)
+    per_shot = int((4 * k * b + 2 * b).sum())
+    return (coef + nshots * per_shot) * word
 
 
 # ---------------------------------------------------------------------------
@@ -185,6 +209,10 @@ def time_oracle(p, rs, dt, dtf, nsteps_sample):
 
 def reference_arm(args, rank, world):
     if rank != 0:
+        return
+    if args.workload != "cfg2":
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm is sized for the "
+                          "config-2 workload; building the config-3 ROMs on the host is not a bounded sample"}))
         return
     p, rs, dt, dtf = oracle_sample(args.cpu_sample_steps)
     ns = args.cpu_sample_steps
@@ -228,7 +256,7 @@ def main():
         dist.init_process_group("nccl")
     from paper_1406_6923_gb300 import sfm
 
-    p = inputs.config2()
+    p = inputs.config2() if args.workload == "cfg2" else inputs.config3()
     nsteps = args.nsteps or p.nsteps
     stream = torch.cuda.current_stream()
     h = sfm.sfm_create(local)
@@ -310,6 +338,10 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     ncell = p.nx * p.ny * p.nz
+    bw = face_modes(p).sum(axis=1)
+    widths = int(bw[0]) if bw.min() == bw.max() else [int(bw.min()), int(bw.max())]
+    kk = np.asarray(p.k_sub)
+    levels = int(kk[0]) if kk.min() == kk.max() else [int(kk.min()), int(kk.max())]
     per_rank = ncell * nsteps * (dt / dtf) * nshots / (ms * 1e-3)
     value = per_rank * world
 
@@ -328,17 +360,17 @@ def main():
     # roofline of the persistent stepping kernel
     pk, pk_kind = peaks()
     word = {"fp32f": 4, "fp32": 4, "fp32x2": 8, "fp64": 8}[chosen]
-    bytes_step = algorithmic_bytes_per_step(p.nsub, 48, 16, 8, count_rpairs(sfm, h, p), word)
+    bytes_step = algorithmic_bytes_per_step(p, nshots, receiver_row_numbers(p), word)
     kms = statistics.mean(kern_ms)
     achieved = bytes_step * nsteps / (kms * 1e-3) / 1e9
-    traffic = read_traffic()
+    traffic = read_traffic() if args.workload == "cfg2" else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
             "peak_source": f"{pk_kind} HBM copy", "kernel": "step_kernel",
             "kernel_ms": kms, "bytes_per_time_step": bytes_step}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "cfg2":
         po, rs, dto, dtfo = oracle_sample(args.cpu_sample_steps)
         v, wall_c, cores = time_oracle(po, rs, dto, dtfo, args.cpu_sample_steps)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -350,7 +382,8 @@ def main():
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": {"fp32f": "f32", "fp32": "f32", "fp32x2": "f32x2", "fp64": "f64"}[chosen],
            "data": "synthetic",
-           "config": {"workload": p.name, "cells": ncell, "subdomains": p.nsub, "b": 48, "k": 16,
+           "config": {"workload": p.name, "cells": ncell, "subdomains": p.nsub,
+                      "b": widths, "k": levels,
                       "shots": nshots, "receivers": nrec, "time_steps": nsteps,
                       "precision": chosen, "trace_err_vs_fp64": errors,
                       "dt": dt, "dt_fine": dtf, "dt_ratio": dt / dtf,
@@ -371,10 +404,13 @@ def main():
         dist.destroy_process_group()
 
 
-def count_rpairs(sfm, h, p):
-    """Receiver (receiver, subdomain) pairs of the workload: a receiver on a
-    node shared by several subdomains has one pair per subdomain."""
+def receiver_row_numbers(p):
+    """Numbers in all receiver rows: one row of k*b per (receiver, subdomain)
+    pair, a receiver on a node shared by several subdomains having one pair
+    per subdomain."""
     xs = [np.asarray(p.xcuts), np.asarray(p.ycuts), np.asarray(p.zcuts)]
+    ncx, ncy = len(p.xcuts) - 1, len(p.ycuts) - 1
+    kb = face_modes(p).sum(axis=1) * np.asarray(p.k_sub)
     n = 0
     for x in p.rec_xyz:
         nodes, w = inputs.trilinear_node_weights(x, p.h, p.nx, p.ny, p.nz)
@@ -384,8 +420,8 @@ def count_rpairs(sfm, h, p):
             for i in cand[0]:
                 for j in cand[1]:
                     for k in cand[2]:
-                        subs.add((i, j, k))
-        n += len(subs)
+                        subs.add(int(i + ncx * (j + ncy * k)))
+        n += int(sum(kb[s] for s in subs))
     return n
 
 

@@ -208,6 +208,8 @@ typedef struct sfm_build_report {
     double cg_residual_max;    /* worst final relative residual of the solves    */
     double krylov_min_ratio;   /* smallest min/max diag of a Krylov block's R    */
     int nclasses;              /* subdomain shape classes built as batches       */
+    int nregularized;          /* blocks projected on the semi-definite cone
+                                  (deep levels singular at FP64 rounding level)  */
 } sfm_build_report;
 
 /*
@@ -217,7 +219,12 @@ typedef struct sfm_build_report {
  * F itself as the first block, each solve a Jacobi-preconditioned CG to the
  * relative residual cg_tol, block Gram-Schmidt twice), L~ = V^T L V,
  * F~ = V^T F (Eq. 5), block Lanczos on (L~, F~) with full
- * reorthogonalisation (Eq. 8) and the recursion of Eq. 13.  Sets the
+ * reorthogonalisation (Eq. 8) and the recursion of Eq. 13.  Every finished
+ * block is test-factored in FP64; one with a non-positive pivot (a deep
+ * level whose smallest eigenvalues sit at the rounding level, some of them
+ * rounded below zero) is replaced by its projection on the positive
+ * semi-definite cone (negative eigenvalues set to 0; counted in
+ * rep->nregularized).  Sets the
  * topology and coefficients exactly as sfm_set_topology + sfm_set_coeffs
  * would.  m_sub[nsub], k_sub[nsub]: modes per face and levels per subdomain.
  * Errors: SFM_ERR_STATE (no model), SFM_ERR_ARG (block width above 64 or

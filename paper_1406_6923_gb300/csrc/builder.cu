@@ -519,6 +519,25 @@ extern "C" int sfm_build_roms(sfm_handle* h, const int* m_sub, const int* k_sub,
         return bfail(h, herr, herr == SFM_ERR_NOT_SPD ? "sfm_build_roms: Gamma_j not positive definite"
                                                       : "sfm_build_roms: breakdown in a block factorisation");
     }
+    // blocks that are semi-definite only up to FP64 rounding: projected on
+    // the positive semi-definite cone (counted in the report)
+    int nreg = 0;
+    {
+        int* d_nreg = nullptr;
+        BCK(h, dmalloc(d_nreg, 1));
+        BCK(h, cudaMemsetAsync(d_nreg, 0, sizeof(int), st));
+        BCK(h, cudaFuncSetAttribute(sfm::psd_project_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sfm::PSD_SMEM));
+        for (int s0 = 0; s0 < h->nsub; s0 += 65535) {
+            const int ns = std::min(65535, h->nsub - s0);
+            sfm::psd_project_kernel<<<dim3(2 * h->kmax, ns), 256, sfm::PSD_SMEM, st>>>(
+                d_coef, h->d_coef_off + s0, h->d_b + s0, h->d_k + s0, d_nreg);
+        }
+        BCK(h, cudaGetLastError());
+        BCK(h, cudaMemcpyAsync(&nreg, d_nreg, sizeof(int), cudaMemcpyDeviceToHost, st));
+        BCK(h, cudaStreamSynchronize(st));
+        dfree(d_nreg);
+    }
     rc = sfm::set_coeffs_device(h, d_coef);
     dfree(d_coef);
     if (rc) return rc;
@@ -529,6 +548,7 @@ extern "C" int sfm_build_roms(sfm_handle* h, const int* m_sub, const int* k_sub,
         rep->cg_residual_max = cg_res_max;
         rep->krylov_min_ratio = min_ratio;
         rep->nclasses = (int)B->classes.size();
+        rep->nregularized = nreg;
     }
     return SFM_OK;
 }

@@ -500,4 +500,116 @@ __global__ void finish_project_kernel(const double* Z, const double* Ginv, int b
 }
 
 }  // namespace bld
+
+// Positive semi-definiteness of the finished S-fraction blocks (FP64
+// masters, per subdomain Gamma_1..k then Gammahat_1..k, b x b).  One block
+// of threads per (subdomain, block).  A Cholesky test in shared memory
+// leaves a block that factors untouched; a block that meets a non-positive
+// pivot (deep levels whose smallest eigenvalues sit at the FP64 rounding
+// level, where rounding makes some slightly negative) is replaced by its
+// projection on the positive semi-definite cone, V max(Lambda, 0) V^T, from
+// a cyclic Jacobi eigen-decomposition; such blocks are counted.  A shift
+// would be wrong here: it gives a singular inverse-mass direction a finite
+// mass, and with the large stiffness paired with it a spurious fast mode.
+constexpr int REG_LD = 65;
+constexpr size_t PSD_SMEM = 2 * 64 * REG_LD * sizeof(double);
+__global__ void __launch_bounds__(256) psd_project_kernel(double* coef, const long long* coef_off,
+                                                          const int* sub_b, const int* sub_k,
+                                                          int* nproj) {
+    extern __shared__ double psd_smem[];      // A and V, 64 x REG_LD each
+    double* A = psd_smem;
+    double* V = psd_smem + 64 * REG_LD;
+    __shared__ double s_cs[2];
+    __shared__ int s_ok;
+    const int s = blockIdx.y, blk = blockIdx.x;
+    const int b = sub_b[s], k = sub_k[s];
+    if (blk >= 2 * k) return;
+    double* m = coef + coef_off[s] + (long long)blk * b * b;
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) A[(e / b) * REG_LD + e % b] = m[e];
+    // Cholesky test
+    bool ok = true;
+    for (int c = 0; c < b; ++c) {
+        __syncthreads();
+        const double d = A[c * REG_LD + c];
+        if (!(d > 0.0)) { ok = false; break; }
+        const double l = sqrt(d);
+        __syncthreads();
+        if (threadIdx.x == 0) A[c * REG_LD + c] = l;
+        for (int i = c + 1 + threadIdx.x; i < b; i += blockDim.x) A[i * REG_LD + c] /= l;
+        __syncthreads();
+        const int n = b - c - 1;
+        for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+            const int i = c + 1 + t / n, jj = c + 1 + t % n;
+            if (jj <= i) A[i * REG_LD + jj] -= A[i * REG_LD + c] * A[jj * REG_LD + c];
+        }
+    }
+    __syncthreads();
+    if (ok) return;
+    // cyclic Jacobi on the symmetrised block
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+        const int i = e / b, j = e % b;
+        A[i * REG_LD + j] = 0.5 * (m[i * b + j] + m[j * b + i]);
+        V[i * REG_LD + j] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int sweep = 0; sweep < 30; ++sweep) {
+        if (threadIdx.x == 0) {
+            double off = 0.0, dia = 0.0;
+            for (int i = 0; i < b; ++i)
+                for (int j = 0; j < b; ++j)
+                    (i == j ? dia : off) += A[i * REG_LD + j] * A[i * REG_LD + j];
+            s_ok = (off <= 1e-30 * dia) ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_ok) break;
+        for (int pp = 0; pp < b - 1; ++pp) {
+            for (int qq = pp + 1; qq < b; ++qq) {
+                if (threadIdx.x == 0) {
+                    const double apq = A[pp * REG_LD + qq];
+                    double c = 1.0, sn = 0.0;
+                    if (apq != 0.0) {
+                        const double tau = (A[qq * REG_LD + qq] - A[pp * REG_LD + pp]) / (2.0 * apq);
+                        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                        c = 1.0 / sqrt(1.0 + t * t);
+                        sn = t * c;
+                    }
+                    s_cs[0] = c;
+                    s_cs[1] = sn;
+                }
+                __syncthreads();
+                const double c = s_cs[0], sn = s_cs[1];
+                if (sn != 0.0) {
+                    // A <- J^T A J on rows and columns pp, qq; V <- V J
+                    for (int i = threadIdx.x; i < b; i += blockDim.x) {
+                        const double aip = A[i * REG_LD + pp], aiq = A[i * REG_LD + qq];
+                        A[i * REG_LD + pp] = c * aip - sn * aiq;
+                        A[i * REG_LD + qq] = sn * aip + c * aiq;
+                        const double vip = V[i * REG_LD + pp], viq = V[i * REG_LD + qq];
+                        V[i * REG_LD + pp] = c * vip - sn * viq;
+                        V[i * REG_LD + qq] = sn * vip + c * viq;
+                    }
+                    __syncthreads();
+                    for (int j = threadIdx.x; j < b; j += blockDim.x) {
+                        const double apj = A[pp * REG_LD + j], aqj = A[qq * REG_LD + j];
+                        A[pp * REG_LD + j] = c * apj - sn * aqj;
+                        A[qq * REG_LD + j] = sn * apj + c * aqj;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+    // m = V max(diag A, 0) V^T
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+        const int i = e / b, j = e % b;
+        double acc = 0.0;
+        for (int t = 0; t < b; ++t) {
+            const double lam = A[t * REG_LD + t];
+            if (lam > 0.0) acc += V[i * REG_LD + t] * lam * V[j * REG_LD + t];
+        }
+        m[e] = acc;
+    }
+    if (threadIdx.x == 0) atomicAdd(nproj, 1);
+}
+
 }  // namespace sfm

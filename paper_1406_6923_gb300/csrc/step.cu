@@ -1062,9 +1062,11 @@ cudaError_t launch_pack_tiles(const double* master, const long long* master_off,
 // 2j, Gammahat_j block 2j+1 (the level-major order of the packed tiles).
 // The b x b FP64 block is factored in shared memory (right-looking, column
 // by column, in FP64), then rounded to FP32 into lower-triangular 8x8 tiles.
-// A non-positive pivot in a block the stepping uses (every Gamma_j and
-// Gammahat_j for j >= 2) sets *bad; Gammahat_1 is replaced by H_f on the
-// faces and is not needed.
+// A pivot at the rounding level (|d| <= 1e-13 max|diag|, or slightly
+// negative down to -1e-8 max|diag|) is a semi-definite direction: its
+// column of the factor is zero.  A pivot below that in a block the stepping
+// uses (every Gamma_j and Gammahat_j for j >= 2) sets *bad; Gammahat_1 is
+// replaced by H_f on the faces and is not needed.
 constexpr int FAC_LD = 65;
 
 __global__ void __launch_bounds__(256) factor_tiles_kernel(const double* master,
@@ -1079,12 +1081,26 @@ __global__ void __launch_bounds__(256) factor_tiles_kernel(const double* master,
     const int j = blk >> 1, which = blk & 1;
     const int nt = (b + 7) / 8, T = nt * (nt + 1) / 2;
     const double* m = master + master_off[s] + ((long long)which * k + j) * b * b;
+    __shared__ double s_scale;
     for (int e = threadIdx.x; e < b * b; e += blockDim.x) A[(e / b) * FAC_LD + e % b] = m[e];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sc = 0.0;
+        for (int i = 0; i < b; ++i) sc = fmax(sc, fabs(A[i * FAC_LD + i]));
+        s_scale = sc;
+    }
     bool ok = true;
     for (int c = 0; c < b; ++c) {
         __syncthreads();
-        const double d = A[c * FAC_LD + c];
-        if (!(d > 0.0)) { ok = false; break; }   // same value in every thread
+        const double d = A[c * FAC_LD + c];     // same value in every thread
+        if (!(d > 1e-13 * s_scale)) {
+            // a semi-definite block (singular to rounding): zero pivot, zero
+            // column; a clearly negative pivot means the block is indefinite
+            if (!(d >= -1e-8 * s_scale)) { ok = false; break; }
+            __syncthreads();
+            for (int i = c + threadIdx.x; i < b; i += blockDim.x) A[i * FAC_LD + c] = 0.0;
+            continue;
+        }
         const double l = sqrt(d);
         __syncthreads();
         if (threadIdx.x == 0) A[c * FAC_LD + c] = l;

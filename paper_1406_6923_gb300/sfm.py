@@ -42,7 +42,7 @@ EXPORTS = ["sfm_create", "sfm_destroy", "sfm_last_error", "sfm_set_stream", "sfm
 class sfm_build_report(C.Structure):
     _fields_ = [("seconds", C.c_double), ("cg_iterations_max", C.c_int),
                 ("cg_residual_max", C.c_double), ("krylov_min_ratio", C.c_double),
-                ("nclasses", C.c_int)]
+                ("nclasses", C.c_int), ("nregularized", C.c_int)]
 
 
 class SfmError(RuntimeError):

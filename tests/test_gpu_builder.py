@@ -63,6 +63,8 @@ def test_builder_coefficients_match_oracle(sfm, uneven_problem):
     finally:
         sfm.sfm_destroy(h)
     assert rep["cg_residual_max"] < 1e-13
+    # well-conditioned ROMs need no diagonal shift
+    assert rep["nregularized"] == 0
     for s in range(rs.nsub):
         G, Gh = got[s]
         for j in range(rs.k[s]):
