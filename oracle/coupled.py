@@ -93,13 +93,20 @@ def _groups(rs):
     return [(np.array(v), b, k) for (b, k), v in keys.items()]
 
 
-def step_structured(rs, dt, nsteps, wavelet):
+def step_structured(rs, dt, nsteps, wavelet, U0=None, V0=None):
     """Coupled leapfrog of all subdomain ROMs (Algorithm 1 stage 2).
 
     ``wavelet``: [nshots, nsteps] samples ``f(t_n)``.  Returns traces
     ``[nshots, nrec, nsteps+1]`` (float64).  The state is one flat array:
     the face blocks first, then the levels 2..k of every subdomain, grouped
-    by (b, k) so each group's levels are a (S, k-1, b, shots) view."""
+    by (b, k) so each group's levels are a (S, k-1, b, shots) view.
+
+    ``U0``, ``V0``: optional initial state and time derivative (Algorithm 1
+    step 1.4), per shot a dict subdomain -> (k, b) rows (``rs.U0``/``rs.V0``
+    of ``pipeline.build``); missing entries are zero.  The start is the
+    second-order Taylor step ``U^1 = U^0 + dt V^0 + dt^2/2 a_hom(U^0) +
+    dt^2 p f(t_0)``, i.e. ``delta^0 = dt V^0 - dt^2/2 a_hom(U^0)`` in the
+    increment form (``a_hom``: the right-hand side without the source)."""
     topo = rs.topo
     nsh = rs.nshots
     wavelet = np.asarray(wavelet, dtype=np.float64).reshape(nsh, -1)
@@ -135,13 +142,11 @@ def step_structured(rs, dt, nsteps, wavelet):
             vv.append(row.ravel())
     R = sp.csr_matrix((np.concatenate(vv) if vv else [], (np.concatenate(rr) if rr else [],
                        np.concatenate(cc) if cc else [])), shape=(rs.nrec, ndof))
-    X = np.zeros((ndof, nsh))                   # U
-    dX = np.zeros((ndof, nsh))                  # delta
     Hblk = sp.block_diag([sp.csr_matrix(x) for x in rs.H], format="csr")
-    out = np.zeros((nsh, rs.nrec, nsteps + 1))
-    for it in range(nsteps):
-        out[:, :, it] = (R @ X).T
-        w = wavelet[:, it]
+
+    def accel(X, w):
+        """Right-hand sides of Eqs. 18-19 at state X with source samples w."""
+        a = np.zeros_like(X)
         Uf = X[:nfm]
         face_sum = np.zeros((nfm, nsh))
         for g in groups:
@@ -155,10 +160,34 @@ def step_structured(rs, dt, nsteps, wavelet):
             # (2.1) face data [phi_1 + p_1 f]_f, summed over both sides of a face
             np.add.at(face_sum, g["idx1"], phi[:, 0] + src[:, 0])
             # (2.2) interior levels, Eq. (19)
-            a = np.matmul(g["Gh"], phi[:, 1:] - phi[:, :-1] + src[:, 1:])
-            dX[g["lo"]:g["hi"]] += dt * dt * a.reshape(-1, nsh)
+            ai = np.matmul(g["Gh"], phi[:, 1:] - phi[:, :-1] + src[:, 1:])
+            a[g["lo"]:g["hi"]] = ai.reshape(-1, nsh)
         # (2.3) faces, Eq. (18)
-        dX[:nfm] += dt * dt * (Hblk @ face_sum)
+        a[:nfm] = Hblk @ face_sum
+        return a
+
+    def flat(rows):
+        """Per-shot dicts of (k, b) rows -> the flat state (face blocks are
+        shared: both sides carry the same values)."""
+        X = np.zeros((ndof, nsh))
+        for q in range(min(nsh, len(rows))):
+            for s, row in rows[q].items():
+                g = groups[where[s][0]]
+                i, b, k = where[s][1], g["b"], g["k"]
+                X[g["idx1"][i], q] = row[0]
+                X[g["lo"] + i * (k - 1) * b:g["lo"] + (i + 1) * (k - 1) * b, q] = row[1:].ravel()
+        return X
+
+    X = np.zeros((ndof, nsh)) if U0 is None else flat(U0)         # U
+    dX = np.zeros((ndof, nsh))                                     # delta
+    if V0 is not None:
+        dX += dt * flat(V0)
+    if U0 is not None:
+        dX -= 0.5 * dt * dt * accel(X, np.zeros(nsh))
+    out = np.zeros((nsh, rs.nrec, nsteps + 1))
+    for it in range(nsteps):
+        out[:, :, it] = (R @ X).T
+        dX += dt * dt * accel(X, wavelet[:, it])
         X += dX
     out[:, :, nsteps] = (R @ X).T
     return out

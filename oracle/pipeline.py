@@ -36,12 +36,21 @@ class SubdomainROM:
         """Projected rows (k, b) of a nodal vector (Algorithm 1 step 1.4)."""
         return project.project(self._V, self._Qh, self.G, self.mass, vec)
 
+    def state_rows(self, u):
+        """S-fraction coordinates (k, b) of a nodal field on the box
+        (Algorithm 1 step 1.4, Eq. 16)."""
+        return project.project_state(self._V, self._Qh, self.G, self.mass, u)
 
 
-def build(problem, keep=False, subs=None):
+
+def build(problem, keep=False, subs=None, u0=None, v0=None):
     """Build the ROM set of ``problem``.  ``keep`` keeps every subdomain's
     ``SubdomainROM`` (with V) in ``.subroms``; ``subs`` restricts the build
     to a list of subdomains (their coefficients only, for sampling).
+    ``u0``, ``v0``: initial displacement and velocity, nodal arrays
+    [shot][nz+1][ny+1][nx+1] (or without the shot axis for one shot);
+    their S-fraction coordinates go to ``rs.U0``, ``rs.V0`` (per shot, a
+    dict subdomain -> (k, b)).
 
     Subdomains whose operator inputs are identical (same box shape, same
     velocity block, same face mode counts, same k) have identical ROMs; the
@@ -58,6 +67,16 @@ def build(problem, keep=False, subs=None):
     rec = [dict() for _ in rec_w]
     kept = {}
     built = {}
+    inits = []
+    for field in (u0, v0):
+        if field is None:
+            inits.append(None)
+            continue
+        f = np.asarray(field, dtype=np.float64)
+        inits.append(f[None] if f.ndim == 3 else f)
+    ninit = max((x.shape[0] for x in inits if x is not None), default=0)
+    U0 = [dict() for _ in range(ninit)]
+    V0 = [dict() for _ in range(ninit)]
     for s in (range(problem.nsub) if subs is None else subs):
         box = problem.sub_box(s)
         x0, x1, y0, y1, z0, z1 = box
@@ -83,11 +102,17 @@ def build(problem, keep=False, subs=None):
             rows = sr.rows(np.stack(vecs, axis=1))
             for (dst, i), row in zip(where, rows):
                 dst[i][s] = row
+        for field, dst in zip(inits, (U0, V0)):
+            if field is None:
+                continue
+            for q in range(field.shape[0]):
+                dst[q][s] = sr.state_rows(field[q, z0:z1 + 1, y0:y1 + 1, x0:x1 + 1].ravel())
         if keep:
             kept[s] = sr
     if subs is not None:
         return topo, Gam, Gh, kept
     rs = coupled.RomSet(topo, Gam, Gh, src, rec)
+    rs.U0, rs.V0 = U0, V0
     rs.subroms = kept
     rs.distinct = len(built)
     return rs

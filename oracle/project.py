@@ -11,6 +11,12 @@ The change of variables is Eq. (16), ``U_j = G_j [Qh^T V^T w]_j`` with
   so a receiver that reads ``e^T u`` reads ``sum_j rho_j^T U_j`` with
   ``rho_j = G_j^{-T} Qh_j^T V^T M^{-1/2} e``.
 
+Initial conditions (Algorithm 1 step 1.4 as the paper states it): a nodal
+field u (a displacement, or a velocity for the time derivative) maps to
+``U_j = G_j [Qh^T V^T M^{1/2} u]_j`` (``project_state``).  On the level-1
+face blocks this is ``B^T u`` (the first Krylov block is F and
+``G_1 = R_1^T``), so the two sides of a shared face agree.
+
 Readings where the paper is silent (its experiment uses an initial pulse,
 Algorithm 1 step 1.4; the workloads here use a point force):
 
@@ -55,3 +61,17 @@ def project(V, Qh, G, sub_mass, vec):
     out = np.stack([np.linalg.solve(G[j].T, Y[j * b:(j + 1) * b]) for j in range(k)])  # (k,b,n)
     out = np.moveaxis(out, 2, 0)
     return out[0] if one else out
+
+
+def project_state(V, Qh, G, sub_mass, u):
+    """Eq. (16) applied to a nodal field: ``U_j = G_j [Qh^T V^T M^{1/2} u]_j``
+    for j = 1..k; returns (k, b).  ``u`` may be a matrix of columns (N, n):
+    returns (n, k, b)."""
+    one = u.ndim == 1
+    X = u[:, None] if one else u
+    Y = Qh.T @ (V.T @ (X * np.sqrt(sub_mass)[:, None]))
+    b = G[0].shape[0]
+    out = np.stack([G[j] @ Y[j * b:(j + 1) * b] for j in range(len(G))])    # (k, b, n)
+    out = np.moveaxis(out, 2, 0)
+    return out[0] if one else out
+
