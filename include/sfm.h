@@ -133,7 +133,26 @@ int sfm_set_receivers(sfm_handle* h, int nrec, int npairs, const int* pair_rec,
                       const int* pair_sub, const double* rows);
 
 /*
- * Coupled leapfrog time stepping (Algorithm 1 stage 2): from rest, for
+ * Initial state of the coupled stepping (Algorithm 1 step 1.4 for initial
+ * conditions; Stage 2 starts from U_j|t=0 and dU_j/dt|t=0): per (shot,
+ * subdomain) pair a row block u0_rows[k_s][b_s] of U_j(0) and, unless
+ * v0_rows is NULL (zero velocity), one of dU_j/dt(0), both FP64, pairs
+ * concatenated in the order given; pairs not listed start at rest.  For a
+ * nodal field u the rows are U_j = G_j [Qh^T V^T M^{1/2} u]_j (Eq. 16).
+ * sfm_run then starts with U^0 and the increment
+ *     delta^0 = dt V^0 - dt^2/2 a_hom(U^0)
+ * (the second-order Taylor start; a_hom: the right-hand side of Eqs.
+ * 18-19 without the source, evaluated in FP64 on the GPU).  nshots must
+ * equal the sources' shot count at sfm_run.  npairs = 0 clears the initial
+ * state.  Host arrays, copied.  Errors: SFM_ERR_ARG, SFM_ERR_STATE (no
+ * topology).  sfm_run_static always starts from rest.
+ */
+int sfm_set_initial(sfm_handle* h, int nshots, int npairs, const int* pair_shot,
+                    const int* pair_sub, const double* u0_rows, const double* v0_rows);
+
+/*
+ * Coupled leapfrog time stepping (Algorithm 1 stage 2): from rest (or from
+ * the state of sfm_set_initial), for
  * n = 0..nsteps-1 the right-hand sides of Eqs. 18-19 (with the source term
  * f_q(t_n)) are evaluated at t_n = n*dt and
  *     delta^{n+1} = delta^n + dt^2 a^n,  U^{n+1} = U^n + delta^{n+1}.

@@ -163,7 +163,7 @@ int sfm_destroy(sfm_handle* h) {
     dfree(h->d_tcoef_off);
     dfree(h->d_coef64); dfree(h->d_H64); dfree(h->d_src64); dfree(h->d_src_off);
     dfree(h->d_rrows64); dfree(h->d_rp_sub); dfree(h->d_rec_ptr); dfree(h->d_rec_pairs);
-    dfree(h->d_frow); dfree(h->d_rtab);
+    dfree(h->d_frow); dfree(h->d_rtab); dfree(h->d_init_U64); dfree(h->d_init_V64);
     dfree(h->d_rp_off); dfree(h->d_bar); dfree(h->d_err);
     if (h->stream && h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -267,7 +267,7 @@ int sfm_set_topology(sfm_handle* h, int nsub, const int* k_sub, const int* m_fac
             return fail(h, SFM_ERR_ARG, "sfm_set_topology: offsets beyond 32 bits");
         CK(h, upload(h->d_frow, rows.data(), rows.size(), st));
     }
-    h->have_coef = h->have_src = h->have_rec = false;
+    h->have_coef = h->have_src = h->have_rec = h->have_init = false;
     invalidate(h);
     return SFM_OK;
 }
@@ -366,6 +366,44 @@ int sfm_set_sources(sfm_handle* h, int nshots, int npairs, const int* pair_shot,
     h->have_src = true;
     ext(h)->piece_grid = -1;   // piece records carry the source offsets
     invalidate(h);
+    return SFM_OK;
+}
+
+int sfm_set_initial(sfm_handle* h, int nshots, int npairs, const int* pair_shot,
+                    const int* pair_sub, const double* u0_rows, const double* v0_rows) {
+    if (!h) return fail(nullptr, SFM_ERR_ARG, "NULL handle");
+    if (h->nsub == 0) return fail(h, SFM_ERR_STATE, "sfm_set_initial: no topology");
+    if (nshots < 0 || npairs < 0 || (npairs > 0 && (!pair_shot || !pair_sub || !u0_rows)))
+        return fail(h, SFM_ERR_ARG, "sfm_set_initial: bad arguments");
+    CK(h, cudaSetDevice(h->device));
+    if (npairs == 0) {
+        h->have_init = false;
+        return SFM_OK;
+    }
+    std::vector<double> U((size_t)nshots * h->nstate, 0.0), V;
+    if (v0_rows) V.assign(U.size(), 0.0);
+    std::vector<char> seen((size_t)nshots * h->nsub, 0);
+    long long o = 0;
+    for (int i = 0; i < npairs; ++i) {
+        const int q = pair_shot[i], s = pair_sub[i];
+        if (q < 0 || q >= nshots || s < 0 || s >= h->nsub)
+            return fail(h, SFM_ERR_ARG, "sfm_set_initial: pair index out of range");
+        if (seen[(size_t)q * h->nsub + s]++)
+            return fail(h, SFM_ERR_ARG, "sfm_set_initial: duplicate (shot, subdomain) pair");
+        const long long kb = (long long)h->k[s] * h->b[s];
+        const size_t at = (size_t)q * h->nstate + h->state_off[s];
+        std::copy(u0_rows + o, u0_rows + o + kb, U.begin() + at);
+        if (v0_rows) std::copy(v0_rows + o, v0_rows + o + kb, V.begin() + at);
+        o += kb;
+    }
+    CK(h, upload(h->d_init_U64, U.data(), U.size(), h->stream));
+    if (v0_rows) {
+        CK(h, upload(h->d_init_V64, V.data(), V.size(), h->stream));
+    } else {
+        dfree(h->d_init_V64);
+    }
+    h->init_nshots = nshots;
+    h->have_init = true;
     return SFM_OK;
 }
 
@@ -547,6 +585,68 @@ static cudaError_t grow(P*& p, size_t& have, size_t need) {
     return e;
 }
 
+// Right-hand side without the source for every shot of the initial state:
+// one step of the FP64 stepping kernel from state X (state layout, all
+// shots) with zero increment, zero source and dt = 1 leaves a_hom(X) in the
+// increment buffer A.
+static int accel_f64(sfm_handle* h, const double* X, double* A, int* launches) {
+    int rc = prepare<sfm::PolF64>(h);
+    if (rc != SFM_OK) return rc;
+    sfm_ext* x = ext(h);
+    Cache<double>& c = x->c64;
+    cudaStream_t st = h->stream;
+    const int nsh = h->init_nshots;
+    const size_t n = (size_t)nsh * h->nstate;
+    double *U0 = nullptr, *U1 = nullptr, *m0 = nullptr, *m1 = nullptr, *wav = nullptr;
+    unsigned* ctr = nullptr;
+    auto cleanup = [&]() { dfree(U0); dfree(U1); dfree(m0); dfree(m1); dfree(wav); dfree(ctr); };
+#define CKA(call)                                                              \
+    do {                                                                       \
+        cudaError_t e__ = (call);                                              \
+        if (e__ != cudaSuccess) { cleanup(); return cuda_fail(h, e__, #call); } \
+    } while (0)
+    CKA(dalloc(U0, n));
+    CKA(dalloc(U1, n));
+    CKA(dalloc(m0, (size_t)nsh * h->nmail));
+    CKA(dalloc(m1, (size_t)nsh * h->nmail));
+    CKA(dalloc(wav, (size_t)nsh));
+    CKA(dalloc(ctr, 2));
+    CKA(cudaMemcpyAsync(U0, X, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CKA(cudaMemsetAsync(A, 0, n * sizeof(double), st));
+    CKA(cudaMemsetAsync(wav, 0, (size_t)nsh * sizeof(double), st));
+    CKA(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned), st));
+    CKA(cudaMemsetAsync(h->d_bar, 0, sizeof(unsigned int), st));
+    CKA(cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+    sfm::StepParams<double> p{};
+    p.nsub = h->nsub; p.nshots = nsh; p.nunits = nsh * h->nsub; p.nsteps = 1;
+    p.kmax = h->kmax; p.bmax = h->bmax;
+    p.sub_b = h->d_b; p.sub_k = h->d_k; p.coef_off = h->d_tcoef_off; p.coef = c.coef;
+    p.face_off = h->d_face_off; p.nbr = h->d_nbr; p.H_off = h->d_H_off; p.H = c.H;
+    p.state_off = h->d_state_off; p.state_stride = h->nstate;
+    p.U[0] = U0; p.U[1] = U1; p.U[2] = p.U[3] = nullptr;
+    p.dU = A;
+    p.mail_off = h->d_mail_off; p.mail_stride = h->nmail; p.mail0 = m0; p.mail1 = m1;
+    p.src_off = nullptr; p.src = c.src; p.wavelet = wav;
+    p.nrec = 0; p.nrpairs = 0; p.rp_sub = nullptr; p.rp_off = nullptr; p.rrows = nullptr;
+    p.partial = nullptr; p.rctr = ctr;
+    p.dt2 = 1.0;
+    p.bar = h->d_bar; p.err = h->d_err; p.timeout_ns = x->timeout_ns; p.skip_arrive = -1;
+    p.Kx = nullptr;
+    int grid = 0;
+    rc = step_setup<sfm::PolF64>(h, p.nunits, nullptr, p, &grid);
+    if (rc != SFM_OK) { cleanup(); return rc; }
+    p.rtab = nullptr;
+    CKA(sfm::launch_step<sfm::PolF64>(p, grid, st));
+    ++*launches;
+    int herr = 0;
+    CKA(cudaMemcpyAsync(&herr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CKA(cudaStreamSynchronize(st));
+#undef CKA
+    cleanup();
+    if (herr != 0) return fail(h, herr, "initial state: device error");
+    return SFM_OK;
+}
+
 template <class P>
 static int run_impl(sfm_handle* h, double dt, int nsteps, const double* wavelet, double* traces,
                     int flags, double* kernel_ms) {
@@ -590,6 +690,33 @@ static int run_impl(sfm_handle* h, double dt, int nsteps, const double* wavelet,
     for (int i = 0; i < 4; ++i) CK(h, cudaMemsetAsync(r.U[i], 0, nst * sizeof(T), st));
     CK(h, cudaMemsetAsync(r.rctr, 0, ((size_t)nsteps + 1) * sizeof(unsigned), st));
     CK(h, cudaMemsetAsync(r.dU, 0, nst * sizeof(T), st));
+    if (h->have_init) {
+        // Algorithm 1 step 1.4: U^0 given, delta^0 = dt V^0 - dt^2/2 a_hom(U^0)
+        // (the second-order Taylor start in increment form), computed in FP64
+        if (h->init_nshots != h->nshots) {
+            dfree(tmp64);
+            return fail(h, SFM_ERR_STATE, "sfm_run: initial state set for a different shot count");
+        }
+        double *A = nullptr, *D = nullptr;
+        cudaError_t e0 = dalloc(A, nst);
+        if (e0 == cudaSuccess) e0 = dalloc(D, nst);
+        if (e0 != cudaSuccess) { dfree(A); dfree(D); dfree(tmp64); return cuda_fail(h, e0, "initial state"); }
+        rc = accel_f64(h, h->d_init_U64, A, &launches);
+        cudaError_t e1 = cudaSuccess;
+        if (rc == SFM_OK) {
+            if ((e1 = sfm::launch_start_delta(h->d_init_V64, A, dt, nst, D, st)) == cudaSuccess &&
+                (e1 = sfm::launch_convert<P>(h->d_init_U64, r.U[0], nst, st)) == cudaSuccess &&
+                (e1 = sfm::launch_convert<P>(D, r.dU, nst, st)) == cudaSuccess)
+                e1 = cudaStreamSynchronize(st);
+            launches += 3;
+        }
+        dfree(A);
+        dfree(D);
+        if (rc != SFM_OK) { dfree(tmp64); return rc; }
+        if (e1 != cudaSuccess) { dfree(tmp64); return cuda_fail(h, e1, "initial state"); }
+        CK(h, cudaMemsetAsync(h->d_bar, 0, sizeof(unsigned int), st));
+        CK(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+    }
     CK(h, cudaMemsetAsync(h->d_bar, 0, sizeof(unsigned int), st));
     CK(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
     CK(h, cudaMemsetAsync(x->d_bad, 0, sizeof(int), st));

@@ -112,6 +112,9 @@ cudaError_t launch_wdot(const double* x, const double* y, const double* w, size_
                         cudaStream_t st);
 cudaError_t launch_scale(const double* x, double* y, size_t n, const double* sumsq,
                          cudaStream_t st);
+// out = dt * v - 0.5 * dt^2 * a (v NULL: zero velocity)
+cudaError_t launch_start_delta(const double* v, const double* a, double dt, size_t n, double* out,
+                               cudaStream_t st);
 
 template <class P>
 cudaError_t launch_reduce_traces(const typename P::S* partial, const int* rec_ptr,
@@ -165,6 +168,12 @@ struct sfm_handle {
     int *d_rp_sub = nullptr, *d_rec_ptr = nullptr, *d_rec_pairs = nullptr;
     long long* d_rp_off = nullptr;
     int4* d_frow = nullptr;            // face rows (face_rows), set with the topology
+    // initial state (sfm_set_initial): U^0 and dU/dt(0) in the state layout,
+    // FP64, for init_nshots shots (V NULL: zero velocity)
+    double* d_init_U64 = nullptr;
+    double* d_init_V64 = nullptr;
+    int init_nshots = 0;
+    bool have_init = false;
     int4* d_rtab = nullptr;            // receiver pair table (readout_table)
     bool have_src = false, have_rec = false;
 

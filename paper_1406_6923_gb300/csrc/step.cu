@@ -1197,6 +1197,21 @@ cudaError_t launch_scale(const double* x, double* y, size_t n, const double* sum
     return cudaGetLastError();
 }
 
+// Starting increment of the initial-value form: delta^0 = dt V^0 - dt^2/2 a.
+__global__ void start_delta_kernel(const double* v, const double* a, double dt, size_t n,
+                                   double* out) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        out[i] = (v ? dt * v[i] : 0.0) - 0.5 * dt * dt * a[i];
+}
+
+cudaError_t launch_start_delta(const double* v, const double* a, double dt, size_t n, double* out,
+                               cudaStream_t st) {
+    size_t g = (n + 255) / 256;
+    start_delta_kernel<<<(int)(g > 4096 ? 4096 : (g ? g : 1)), 256, 0, st>>>(v, a, dt, n, out);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Face coupling H_f = (sum over sides of [Gammahat_1]_f^{-1})^{-1}  (Eq. 18),
 // FP64, one block per (subdomain, face).  Each side computes its own copy

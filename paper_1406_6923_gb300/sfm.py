@@ -36,7 +36,7 @@ EXPORTS = ["sfm_create", "sfm_destroy", "sfm_last_error", "sfm_set_stream", "sfm
            "sfm_set_coeffs", "sfm_get_coeffs", "sfm_set_sources", "sfm_set_receivers",
            "sfm_run", "sfm_cfl_dt", "sfm_last_launches", "sfm_debug_set", "sfm_set_model",
            "sfm_build_roms", "sfm_project_sources", "sfm_project_receivers", "sfm_free_build", "sfm_run_static",
-           "sfm_autotune"]
+           "sfm_autotune", "sfm_set_initial"]
 
 
 class sfm_build_report(C.Structure):
@@ -90,6 +90,7 @@ def load(path=LIB_PATH):
         "sfm_run_static": (_i, [_i, _p, _i, _ip, _ip, _ip, _p, _i, _i, _ip, _ip, _p, _i, _i, _ip,
                                 _ip, _p, C.c_double, _i, _p, _p]),
         "sfm_autotune": (_i, [_p, _i, _i, _ip, _ip, _dp]),
+        "sfm_set_initial": (_i, [_p, _i, _i, _ip, _ip, _dp, _dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -160,6 +161,17 @@ def sfm_set_sources(h, nshots, pair_shot, pair_sub, rows):
     b, bp = _iarr(pair_sub)
     r, rp = _darr(np.asarray(rows).reshape(-1))
     _check(h, load().sfm_set_sources(h, int(nshots), len(a), ap, bp, rp))
+
+
+def sfm_set_initial(h, nshots, pair_shot, pair_sub, u0_rows, v0_rows=None):
+    a, ap = _iarr(pair_shot)
+    b, bp = _iarr(pair_sub)
+    u, up = _darr(np.asarray(u0_rows).reshape(-1))
+    if v0_rows is None:
+        vp = None
+    else:
+        v, vp = _darr(np.asarray(v0_rows).reshape(-1))
+    _check(h, load().sfm_set_initial(h, int(nshots), len(a), ap, bp, up, vp))
 
 
 def sfm_set_receivers(h, nrec, pair_rec, pair_sub, rows):
