@@ -427,11 +427,12 @@ def receiver_row_numbers(p):
 
 def read_traffic():
     """DRAM bytes per launch of the stepping kernel from the committed ncu
-    summary, when it was taken on the current kernel source (else None)."""
+    summary, when it was taken on the current kernel source (the kernel's
+    own file and the number policies; else None)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "step_kernel_config2.md")
     src = b""
-    for f in ("step.cu", "numeric.cuh"):
+    for f in ("step_kernel.cuh", "numeric.cuh"):
         with open(os.path.join(ROOT, "paper_1406_6923_gb300", "csrc", f), "rb") as fh:
             src += fh.read()
     digest = hashlib.sha256(src).hexdigest()[:16]
