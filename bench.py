@@ -145,6 +145,23 @@ def peaks():
         return {"hbm_gbs": FALLBACK_HBM}, "fallback"
 
 
+def max_over_ranks(x, dist, device):
+    """Largest value of x over the ranks of the process group (x itself
+    without one): the job's time is its slowest rank's."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, ms, world):
+    """Units all ranks processed per second when each of ``world`` replicas
+    processes ``units_per_rank`` in ``ms`` milliseconds (the slowest)."""
+    return units_per_rank * world / (ms * 1e-3)
+
+
 def face_modes(p):
     """Modes per (subdomain, face) of a problem: a shared face carries the
     smaller of its two subdomains' m, an outer face its own (the layout rule
@@ -329,21 +346,18 @@ def main():
             kern_ms.append(run(prec))
             ev[i][1].record(stream)
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         wall = time.perf_counter() - wall0
     launches = sfm.sfm_last_launches(h) * args.steps
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = statistics.mean(step_ms)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(statistics.mean(step_ms), dist, "cuda")
     ncell = p.nx * p.ny * p.nz
     bw = face_modes(p).sum(axis=1)
     widths = int(bw[0]) if bw.min() == bw.max() else [int(bw.min()), int(bw.max())]
     kk = np.asarray(p.k_sub)
     levels = int(kk[0]) if kk.min() == kk.max() else [int(kk.min()), int(kk.max())]
-    per_rank = ncell * nsteps * (dt / dtf) * nshots / (ms * 1e-3)
-    value = per_rank * world
+    value = whole_job_rate(ncell * nsteps * (dt / dtf) * nshots, ms, world)
 
     # end to end through the public API with host buffers (H2D of the
     # wavelet and D2H of the traces inside the timed region)

@@ -308,6 +308,19 @@ int sfm_run_static(int device, void* stream, int nsub, const int* k_sub, const i
                    int nrec_pairs, const int* rec_id, const int* rec_sub, const double* rec_rows,
                    double dt, int nsteps, const double* wavelet, double* traces);
 
+/*
+ * The stepping kernel's work partition (host logic only, no device work; no
+ * counterpart in the paper): the (unit, level) sequence of nunits units,
+ * unit u having k_sub[u % nsub] levels, cut into contiguous pieces for
+ * `grid` blocks so that the blocks' estimated costs are even; a unit is
+ * never cut at level 1.  Outputs: ptr[grid+1] (the pieces of block c are
+ * ptr[c] .. ptr[c+1]-1) and pieces[3*i .. 3*i+2] = (unit, j0, j1), levels
+ * j0 .. j1-1.  *npieces receives the number of pieces; SFM_ERR_ARG if it
+ * exceeds max_pieces (nothing written to pieces) or an argument is bad.
+ */
+int sfm_plan_pieces(int nunits, int nsub, const int* k_sub, int grid, int* ptr, int* pieces,
+                    int max_pieces, int* npieces);
+
 /* Number of device kernels launched by the last sfm_run. */
 int sfm_last_launches(const sfm_handle* h, int* launches);
 

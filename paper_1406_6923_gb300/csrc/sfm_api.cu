@@ -466,6 +466,27 @@ int sfm_debug_set(sfm_handle* h, int key, long long value) {
     return fail(h, SFM_ERR_ARG, "sfm_debug_set: unknown key");
 }
 
+int sfm_plan_pieces(int nunits, int nsub, const int* k_sub, int grid, int* ptr, int* pieces,
+                    int max_pieces, int* npieces) {
+    if (nunits < 1 || nsub < 1 || nunits % nsub != 0 || !k_sub || grid < 1 || !ptr || !npieces ||
+        max_pieces < 0 || (max_pieces > 0 && !pieces))
+        return fail(nullptr, SFM_ERR_ARG, "sfm_plan_pieces: bad arguments");
+    for (int s = 0; s < nsub; ++s)
+        if (k_sub[s] < 1) return fail(nullptr, SFM_ERR_ARG, "sfm_plan_pieces: k < 1");
+    std::vector<int> p;
+    std::vector<int4> pc;
+    sfm::build_pieces(nunits, nsub, k_sub, grid, p, pc);
+    *npieces = (int)pc.size();
+    std::copy(p.begin(), p.end(), ptr);
+    if ((int)pc.size() > max_pieces) return fail(nullptr, SFM_ERR_ARG, "sfm_plan_pieces: max_pieces too small");
+    for (size_t i = 0; i < pc.size(); ++i) {
+        pieces[3 * i] = pc[i].x;
+        pieces[3 * i + 1] = pc[i].y;
+        pieces[3 * i + 2] = pc[i].z;
+    }
+    return SFM_OK;
+}
+
 int sfm_last_launches(const sfm_handle* h, int* launches) {
     if (!h || !launches) return SFM_ERR_ARG;
     *launches = h->last_launches;

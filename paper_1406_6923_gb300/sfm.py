@@ -36,7 +36,7 @@ EXPORTS = ["sfm_create", "sfm_destroy", "sfm_last_error", "sfm_set_stream", "sfm
            "sfm_set_coeffs", "sfm_get_coeffs", "sfm_set_sources", "sfm_set_receivers",
            "sfm_run", "sfm_cfl_dt", "sfm_last_launches", "sfm_debug_set", "sfm_set_model",
            "sfm_build_roms", "sfm_project_sources", "sfm_project_receivers", "sfm_free_build", "sfm_run_static",
-           "sfm_autotune", "sfm_set_initial"]
+           "sfm_autotune", "sfm_set_initial", "sfm_plan_pieces"]
 
 
 class sfm_build_report(C.Structure):
@@ -91,6 +91,7 @@ def load(path=LIB_PATH):
                                 _ip, _p, C.c_double, _i, _p, _p]),
         "sfm_autotune": (_i, [_p, _i, _i, _ip, _ip, _dp]),
         "sfm_set_initial": (_i, [_p, _i, _i, _ip, _ip, _dp, _dp]),
+        "sfm_plan_pieces": (_i, [_i, _i, _ip, _i, _ip, _ip, _i, _ip]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -214,6 +215,21 @@ def sfm_autotune(h, precision, nsteps=200):
     _check(h, load().sfm_autotune(h, int(precision), int(nsteps), C.byref(ncw), C.byref(nst),
                                   C.byref(us)))
     return ncw.value, nst.value, us.value
+
+
+def sfm_plan_pieces(nunits, k_sub, grid):
+    """Returns (ptr[grid+1], pieces[n][3] as (unit, j0, j1))."""
+    k, kp = _iarr(k_sub)
+    ptr = np.zeros(grid + 1, dtype=np.int32)
+    n = C.c_int(0)
+    rc = load().sfm_plan_pieces(int(nunits), len(k), kp, int(grid), ptr.ctypes.data_as(_ip), None, 0,
+                                C.byref(n))
+    if rc not in (SFM_OK, SFM_ERR_ARG) or n.value <= 0:
+        _check(None, rc)
+    pieces = np.zeros((n.value, 3), dtype=np.int32)
+    _check(None, load().sfm_plan_pieces(int(nunits), len(k), kp, int(grid), ptr.ctypes.data_as(_ip),
+                                        pieces.ctypes.data_as(_ip), n.value, C.byref(n)))
+    return ptr, pieces
 
 
 def sfm_last_launches(h):

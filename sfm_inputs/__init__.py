@@ -317,7 +317,8 @@ def config2(seed=SEED):
 
 def config3(seed=SEED):
     """256x256x128 cells tiled by uneven subdomains (sides from {16,20,24,32}),
-    m in {4,8} and k in 8..24 per subdomain, 64 shots on an 8x8 surface grid,
+    m in {4,8} and k in 8..24 per subdomain (at most 20 where a side is 16
+    cells), 64 shots on an 8x8 surface grid,
     256 receivers on a 16x16 surface grid, 3000 steps (batched, reduced
     precision)."""
     nx, ny, nz, h = 256, 256, 128, 10.0
@@ -327,6 +328,15 @@ def config3(seed=SEED):
     nsub = (len(xc) - 1) * (len(yc) - 1) * (len(zc) - 1)
     m = rng.choice([4, 8], size=nsub)
     k = rng.integers(8, 25, size=nsub)
+    # depth cap on the smallest subdomains: a 16-cell side with k > 20
+    # levels takes the S-fraction coefficients past FP64's dynamic range
+    # (their coupled lambda_max exceeds the Galerkin ROM's)
+    ncx, ncy = len(xc) - 1, len(yc) - 1
+    for s in range(nsub):
+        ix, iy, iz = s % ncx, (s // ncx) % ncy, s // (ncx * ncy)
+        side = min(xc[ix + 1] - xc[ix], yc[iy + 1] - yc[iy], zc[iz + 1] - zc[iz])
+        if side <= 16:
+            k[s] = min(k[s], 20)
     g = (np.arange(8) * 32 + 16) * h
     sx, sy = np.meshgrid(g, g, indexing="ij")
     src = np.stack([sx.ravel(), sy.ravel(), np.full(64, 2 * h)], axis=1)
