@@ -133,3 +133,34 @@ def test_builder_rejects_bad_input(sfm):
         assert e.value.code == sfm.SFM_ERR_ARG
     finally:
         sfm.sfm_destroy(h)
+
+
+@pytest.mark.slow
+def test_builder_full_config2_sampled_against_oracle(sfm):
+    """The full 192^3 layered-lens model with 512 subdomains, m = 8, k = 16,
+    built on the GPU; a sample of subdomains (the source's, a central one, a
+    deep one and a corner) built by the oracle alone.  The transfer
+    functions S(lambda) of the two S-fractions agree at shifts across the
+    source band.  Evaluating S from deep coefficients inverts blocks with
+    condition numbers up to ~1e10 on both sides, so the bound is 1e-6: a
+    wrong block, sign or level gives O(1)."""
+    p = inputs.config2()
+    ncx = len(p.xcuts) - 1
+    sample = [4 + ncx * (4 + ncx * 0), 4 + ncx * (4 + ncx * 4), 2 + ncx * (6 + ncx * 5), 0]
+    topo, Gam, Gh, kept = pipeline.build(p, subs=sample)
+    h = sfm.sfm_create(0)
+    try:
+        sfm.sfm_set_model(h, p.c, p.h, p.xcuts, p.ycuts, p.zcuts)
+        sfm.sfm_build_roms(h, p.m_sub, p.k_sub, p.sigma)
+        coeffs = sfm.sfm_get_coeffs(h)
+    finally:
+        sfm.sfm_destroy(h)
+    b, k = 48, 16
+    per = 2 * k * b * b
+    for s in sample:
+        G = coeffs[s * per:s * per + k * b * b].reshape(k, b, b)
+        H = coeffs[s * per + k * b * b:(s + 1) * per].reshape(k, b, b)
+        for lam in (0.1 * p.sigma, p.sigma, (2 * np.pi * 5 + 2j * np.pi * p.f_peak) ** 2):
+            a = sfrac.transfer_sfraction(list(G), list(H), lam)
+            r = sfrac.transfer_sfraction(list(Gam[s]), list(Gh[s]), lam)
+            assert np.linalg.norm(a - r) / np.linalg.norm(r) < 1e-6, (s, lam)
