@@ -27,7 +27,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // Block layout of the stepping kernel: p.ncw consumer warps do the
 // arithmetic, one producer warp streams the coefficient blocks into shared
 // memory with bulk asynchronous copies (the TMA engine) through a ring of
-// p.nstage stages.  Both are chosen at launch (see step_config).
+// p.nstage stages.  Both are chosen at launch (sfm_autotune picks them).
 constexpr int NCW_MAX = 8;
 constexpr int STEP_BLOCK_MAX = (NCW_MAX + 1) * 32;
 
