@@ -43,10 +43,13 @@ class SubdomainROM:
 
 
 
-def build(problem, keep=False, subs=None, u0=None, v0=None):
+def build(problem, keep=False, subs=None, u0=None, v0=None, depth_tau=None):
     """Build the ROM set of ``problem``.  ``keep`` keeps every subdomain's
     ``SubdomainROM`` (with V) in ``.subroms``; ``subs`` restricts the build
     to a list of subdomains (their coefficients only, for sampling).
+    ``depth_tau``: when given, each subdomain's fraction is cut at
+    ``sfrac.usable_depth(..., depth_tau)`` levels (its source, receiver and
+    initial rows with it; ``rs.k`` then holds the kept depths).
     ``u0``, ``v0``: initial displacement and velocity, nodal arrays
     [shot][nz+1][ny+1][nx+1] (or without the shot axis for one shot);
     their S-fraction coordinates go to ``rs.U0``, ``rs.V0`` (per shot, a
@@ -111,6 +114,12 @@ def build(problem, keep=False, subs=None, u0=None, v0=None):
             kept[s] = sr
     if subs is not None:
         return topo, Gam, Gh, kept
+    if depth_tau is not None:
+        depth = [sfrac.usable_depth(Gam[s], Gh[s], depth_tau) for s in range(problem.nsub)]
+        Gam = [Gam[s][:depth[s]] for s in range(problem.nsub)]
+        Gh = [Gh[s][:depth[s]] for s in range(problem.nsub)]
+        cut = lambda rows: [{s: r[:depth[s]] for s, r in d.items()} for d in rows]
+        src, rec, U0, V0 = cut(src), cut(rec), cut(U0), cut(V0)
     rs = coupled.RomSet(topo, Gam, Gh, src, rec)
     rs.U0, rs.V0 = U0, V0
     rs.subroms = kept

@@ -114,6 +114,28 @@ def gamma_transform(alpha, C, R1, spd_tol=1e-12):
     return Gam, Gh, Gs, mins
 
 
+def usable_depth(Gam, Gh, tau=1e-13):
+    """Number of leading levels whose blocks are positive definite beyond the
+    rounding level: the first level j with ``lambda_min < tau * lambda_max``
+    in Gammahat_j, or in Gamma_j below the last level, ends the usable
+    fraction (at least one level is kept).  Deep levels of an accurate ROM
+    at a small shift run past FP64's dynamic range (their smallest
+    eigenvalues sit at rounding level, some rounded below zero, and the
+    coupled lambda_max of the fraction exceeds the Galerkin ROM's); the
+    fraction truncated there, terminated with U_{j+1} = 0 like the full one,
+    stays a positive definite S-fraction."""
+    k = len(Gam)
+    for j in range(k):
+        eh = np.linalg.eigvalsh(sym(Gh[j]))
+        ok = eh.min() > tau * eh.max()
+        if j < k - 1:
+            eg = np.linalg.eigvalsh(sym(Gam[j]))
+            ok = ok and eg.min() > tau * eg.max()
+        if not ok:
+            return max(j, 1)
+    return k
+
+
 # ----------------------------------------------------------------------------
 # transfer functions S(lambda) = F^T (L + lambda)^{-1} F in its four forms
 # ----------------------------------------------------------------------------

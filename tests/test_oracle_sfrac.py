@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import sfm_inputs as inputs
-from oracle import faces, fine, pipeline, rom, sfrac
+from oracle import coupled, faces, fine, pipeline, rom, sfrac
 
 
 def _single(m=3, k=4, model="random", ncell=(6, 5, 7), seed=3):
@@ -308,3 +308,33 @@ def test_receiver_rows_reproduce_the_galerkin_field(sub):
         assert np.linalg.norm(rom_m - fine_m) < 1e-10 * scale, j
         X = M[:, None] * np.linalg.solve(A, X)
         Y = np.linalg.solve(At, Y)
+
+
+def test_usable_depth_keeps_well_conditioned_fractions_whole():
+    p = inputs.small_problem(ncell=(8, 8, 8), cuts=([0, 8], [0, 8], [0, 8]), m=2, k=4)
+    rs = pipeline.build(p)
+    assert sfrac.usable_depth(rs.Gamma[0], rs.Gammahat[0]) == 4
+    rs2 = pipeline.build(p, depth_tau=1e-13)
+    assert rs2.k[0] == 4
+
+
+@pytest.mark.slow
+def test_usable_depth_cuts_a_fraction_past_fp64_range():
+    """A 16^3-cell subdomain with m = 8 and k = 24 at sigma = (2 pi 8 f)^2:
+    its deep Gammahat blocks are indefinite at rounding level and the
+    fraction's lambda_max exceeds the Galerkin ROM's; cut at its usable
+    depth every block is positive definite and lambda_max is the Galerkin
+    ROM's again (to 1e-3)."""
+    n = 16
+    p = inputs.small_problem(ncell=(n, n, n), cuts=([0, n], [0, n], [0, n]), m=8, k=24,
+                             model="two_layer", f_peak=20.0, sigma=inputs.default_sigma(20.0, 8))
+    full = pipeline.build(p, keep=True)
+    lam_rom = np.linalg.eigvalsh(full.subroms[0].Lt).max()
+    assert coupled.lambda_max(full) > 2.0 * lam_rom
+    cut = pipeline.build(p, depth_tau=1e-13)
+    kk = cut.k[0]
+    assert 1 <= kk < 24
+    for G in list(cut.Gammahat[0]) + list(cut.Gamma[0][:-1]):
+        ev = np.linalg.eigvalsh(G)
+        assert ev.min() > 0
+    assert abs(coupled.lambda_max(cut) / lam_rom - 1.0) < 1e-3
