@@ -42,3 +42,39 @@ def test_dropped_lower_flux_in_the_interior_update_is_caught(monkeypatch):
     monkeypatch.setattr(coupled, "step_structured", bad)
     with pytest.raises(AssertionError):
         init_pins.test_initial_value_stepping_equals_the_assembled_leapfrog(fixture)
+
+
+def test_wrong_sign_in_the_gamma_recursion_is_caught(monkeypatch):
+    """Eq. 13 with +Gamma_{j-1} instead of -Gamma_{j-1}: the block chain no
+    longer returns its blocks."""
+    import test_oracle_sfrac as sfrac_pins
+    from oracle import sfrac
+    sfrac_pins.test_block_chain_gives_back_its_blocks()
+    bad = _mutant(sfrac, "gamma_transform", "Gi.T @ alpha[j] @ Gi - prev", "Gi.T @ alpha[j] @ Gi + prev")
+    monkeypatch.setattr(sfrac, "gamma_transform", bad)
+    with pytest.raises(Exception):
+        sfrac_pins.test_block_chain_gives_back_its_blocks()
+
+
+def test_wrong_edge_conductance_is_caught(monkeypatch):
+    """h/2 instead of h/4 per cell edge: the interior rows are no longer the
+    7-point Laplacian c^2 Delta_h."""
+    import test_oracle_fine as fine_pins
+    from oracle import fine
+    fine_pins.test_uniform_interior_rows_are_7_point_laplacian()
+    bad = _mutant(fine, "assemble", "np.full(ci.shape, h / 4.0)", "np.full(ci.shape, h / 2.0)")
+    monkeypatch.setattr(fine, "assemble", bad)
+    with pytest.raises(AssertionError):
+        fine_pins.test_uniform_interior_rows_are_7_point_laplacian()
+
+
+@pytest.mark.slow
+def test_arithmetic_instead_of_harmonic_face_coupling_is_caught(monkeypatch):
+    """H_f = (sum of the sides' blocks)^{-1} instead of (sum of their
+    inverses)^{-1}: the ROM no longer converges to the slit fine grid."""
+    import test_oracle_coupled as coupled_pins
+    bad = _mutant(coupled, "face_H", "acc = acc + np.linalg.inv(rs.Gammahat[s][0][sl, sl])",
+                  "acc = acc + rs.Gammahat[s][0][sl, sl]")
+    monkeypatch.setattr(coupled, "face_H", bad)
+    with pytest.raises(AssertionError):
+        coupled_pins.test_rom_converges_to_the_slit_fine_grid()
