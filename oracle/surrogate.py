@@ -10,10 +10,10 @@ Pieces, in the order the data flows:
 * a two-layer MLP (ReLU between) to a code z of dimension d;
 * a fixed low-rank decoder r = mu + P z (mean and leading principal
   directions of the training targets, not trained);
-* r -> Cholesky factors of Gamma_j and Gammahat_j for j >= 2, one
-  lower-triangular b x b factor per block with a softplus diagonal, scaled
-  per level: every decoded block is positive definite, so the ROM it gives
-  is a passive S-fraction (Eqs. 12-13) whatever the network outputs;
+* r -> factors of Gamma_j and Gammahat_j for j >= 2, one (unit lower
+  triangular) x diag(exp(g)) factor per block, scaled per level: every
+  decoded block is positive definite, so the ROM it gives is a passive
+  S-fraction (Eqs. 12-13) whatever the network outputs;
 * level 1 from its closed forms, Gammahat_1 = F^T F and
   Gamma_1 = Gammahat_1^{-1} F^T L F Gammahat_1^{-1} (no solves);
 * judged by the NtD map S(lambda) = F^T (L + lambda)^{-1} F, the transfer
@@ -75,19 +75,6 @@ def conv3d_backward(dout, cache, W):
 
 def relu(x):
     return np.maximum(x, 0.0)
-
-
-def softplus(x):
-    return np.logaddexp(0.0, x)
-
-
-def softplus_inv(y):
-    """Inverse of softplus for y > 0."""
-    return y + np.log(-np.expm1(-y))
-
-
-def sigmoid(x):
-    return 0.5 * (1.0 + np.tanh(0.5 * x))
 
 
 # ----------------------------------------------------------------------------
@@ -156,16 +143,21 @@ def features(c, c_ref=2500.0):
 # ----------------------------------------------------------------------------
 
 class FactorDecoder:
-    """Block layout: levels 2..k, each with Gamma_j and Gammahat_j as b x b
-    lower-triangular factors (b(b+1)/2 numbers each, row by row); the
-    diagonal is stored through softplus^{-1}, every factor scaled by a
-    per-(level, kind) constant."""
+    """Block layout: levels 2..k, each with Gamma_j and Gammahat_j written as
+    B = s^2 (U D)(U D)^T, U unit lower triangular, D = diag(exp(g)), s a
+    per-(level, kind) constant; a block's raw numbers are U's entries below
+    the diagonal (row by row) followed by g.  Every raw vector decodes to a
+    positive definite block, and errors are relative per direction (a raw
+    error e moves a pivot by the factor exp(e)), which keeps the NtD map
+    well conditioned in the raw numbers; entrywise errors in the factor
+    itself are not (a 1e-3 error in one Gamma_j factor, relative to its
+    largest entry, can move the NtD map by O(1))."""
 
     def __init__(self, b, k):
         self.b, self.k = b, k
-        self.tri = np.tril_indices(b)
-        self.diag = np.nonzero(self.tri[0] == self.tri[1])[0]
-        self.nper = len(self.tri[0])
+        self.low = np.tril_indices(b, -1)
+        self.nlow = len(self.low[0])
+        self.nper = self.nlow + b
         self.nblocks = 2 * (k - 1)
         self.scale = np.ones(self.nblocks)
         self.mu = None
@@ -175,23 +167,23 @@ class FactorDecoder:
         return [Gam[j] for j in range(1, self.k)] + [Gh[j] for j in range(1, self.k)]
 
     def encode(self, Gam, Gh):
-        """Raw vector of a coefficient set (exact Cholesky factors)."""
+        """Raw vector of a coefficient set (from exact Cholesky factors)."""
         out = []
         for i, B in enumerate(self._blocks(Gam, Gh)):
             L = np.linalg.cholesky(0.5 * (B + B.T)) / self.scale[i]
-            v = L[self.tri].copy()
-            v[self.diag] = softplus_inv(v[self.diag])
-            out.append(v)
+            d = np.diag(L).copy()
+            U = L / d[None, :]
+            out.append(np.concatenate([U[self.low], np.log(d)]))
         return np.concatenate(out)
 
     def blocks(self, r):
-        """Raw vector -> (Gamma_2..k, Gammahat_2..k), each L L^T."""
+        """Raw vector -> (Gamma_2..k, Gammahat_2..k)."""
         mats = []
         for i in range(self.nblocks):
-            v = r[i * self.nper:(i + 1) * self.nper].copy()
-            v[self.diag] = softplus(v[self.diag])
-            L = np.zeros((self.b, self.b))
-            L[self.tri] = v * self.scale[i]
+            v = r[i * self.nper:(i + 1) * self.nper]
+            U = np.eye(self.b)
+            U[self.low] = v[:self.nlow]
+            L = U * (np.exp(v[self.nlow:]) * self.scale[i])[None, :]
             mats.append(L @ L.T)
         return mats[:self.k - 1], mats[self.k - 1:]
 

@@ -107,25 +107,41 @@ def test_level_one_closed_forms(block_rom):
 
 
 def test_decoded_blocks_are_positive_definite(block_rom):
-    """Every raw vector decodes to L L^T with a positive diagonal of L
-    (softplus, even for very negative raw values), i.e. a positive definite
-    block; checked by eigenvalues where L is well conditioned and by the
-    factor's diagonal everywhere."""
+    """Every raw vector decodes to (U D)(U D)^T with U unit lower triangular
+    and D = diag(exp(g)) > 0, i.e. a positive definite block; checked by
+    eigenvalues where the factor is well conditioned and by a Cholesky
+    factorisation with the expected diagonal."""
     p, rs, sr = block_rom
     b, k = rs.b[0], rs.k[0]
     dec = sg.FactorDecoder(b, k)
     rng = np.random.default_rng(5)
-    assert np.all(sg.softplus(np.array([-50.0, -5.0, 0.0, 5.0])) > 0)
     for _ in range(5):
         raw = rng.standard_normal(dec.nblocks * dec.nper)
         for i in range(dec.nblocks):
-            off = np.setdiff1d(np.arange(dec.nper), dec.diag)
-            raw[i * dec.nper + off] *= 0.1          # well-conditioned factors
+            raw[i * dec.nper:i * dec.nper + dec.nlow] *= 0.1      # well-conditioned factors
         G, H = dec.blocks(raw)
-        for B in G + H:
+        for i, B in enumerate(G + H):
             ev = np.linalg.eigvalsh(B)
             assert ev.min() > 1e-6 * ev.max()
-            assert np.all(np.diag(np.linalg.cholesky(B)) > 0)
+            g = raw[i * dec.nper + dec.nlow:(i + 1) * dec.nper]
+            np.testing.assert_allclose(np.diag(np.linalg.cholesky(B)), np.exp(g), rtol=1e-10)
+
+
+def test_decoder_raw_errors_are_relative_per_direction(block_rom):
+    """A raw error of 1e-3 in one block (its unit-lower part and its log
+    pivots) moves the NtD map by about that much, not by O(1)."""
+    p, rs, sr = block_rom
+    b, k = rs.b[0], rs.k[0]
+    dec = sg.FactorDecoder(b, k)
+    r0 = dec.encode(rs.Gamma[0], rs.Gammahat[0])
+    rng = np.random.default_rng(9)
+    G1, H1 = sg.level_one(sr.F, sr.L)
+    for i in range(dec.nblocks):
+        r = r0.copy()
+        r[i * dec.nper:(i + 1) * dec.nper] += 1e-3 * rng.standard_normal(dec.nper)
+        G, H = dec.blocks(r)
+        err = sg.ntd_error([G1] + G, [H1] + H, rs.Gamma[0], rs.Gammahat[0], sg.frequencies(p.f_peak))
+        assert 1e-6 < err < 5e-2, (i, err)
 
 
 def test_fallback_flags_a_wrong_rom_and_passes_the_exact_one(block_rom):
