@@ -92,8 +92,10 @@ int sfm_set_stream(sfm_handle* h, void* stream);
  *   nbr[nsub*6]   neighbour across each face, -1 for an outer face
  *                 (homogeneous Neumann); must be symmetric: if nbr[s][f] = t
  *                 then nbr[t][f^1] = s.
+ * Limits of the stepping kernels: m <= 32 on a face, block width
+ * b_s = sum of the six face counts in 1..64, k_s * b_s <= 16384.
  * Resets coefficients, sources and receivers.
- * Errors: SFM_ERR_ARG for inconsistent topology.
+ * Errors: SFM_ERR_ARG for inconsistent topology or sizes beyond the limits.
  */
 int sfm_set_topology(sfm_handle* h, int nsub, const int* k_sub, const int* m_face,
                      const int* nbr);

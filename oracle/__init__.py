@@ -23,6 +23,10 @@ step by step, in plain NumPy/SciPy float64:
                  update Eq. 19, leapfrog; assembled mass/stiffness, energy and
                  CFL limit.
 * ``pipeline`` - the whole offline stage for a problem from ``sfm_inputs``.
+* ``fidelity`` - trace errors of the coupled ROM against the global and the
+                 slit fine grids (section "Numerical experiments").
+* ``surrogate``- CPU reference of a learned map from a velocity block to its
+                 S-fraction coefficients (an extension of the offline stage).
 
 Every reading of a passage the paper leaves open is stated where it is used.
 """

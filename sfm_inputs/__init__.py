@@ -211,6 +211,36 @@ def salt_bodies(nx, ny, nz, h, rng, nbody=None, c_salt=4500.0):
     return c
 
 
+def skew_fracture(nx, ny, nz, h, rng, c_max=1.0, c_frac=0.3, width=0.08):
+    """A velocity c(x, y) that does not depend on z: 3-4 regions separated by
+    skewed straight lines (values drawn in [0.55, 1] * c_max) crossed by a
+    thin slow fracture, a polyline of three segments (two corners) of the
+    given width at ``c_frac``, so that max(c) / min(c) = c_max / c_frac.
+    Lengths are in the units of ``h``."""
+    x, y, _ = _cell_centres(nx, ny, 1, h)
+    x, y = x[0], y[0]
+    Lx, Ly = nx * h, ny * h
+    nreg = int(rng.integers(3, 5))
+    vals = np.concatenate([[c_max], rng.uniform(0.55, 1.0, nreg - 1) * c_max])
+    rng.shuffle(vals)
+    region = np.zeros(x.shape, int)
+    for y0 in np.sort(rng.uniform(0.15, 0.85, nreg - 1)) * Ly:
+        slope = rng.uniform(-0.4, 0.4)
+        region += (y > y0 + slope * (x - 0.5 * Lx)).astype(int)
+    c2 = vals[region]
+    # fracture: corners at x = Lx/3 and 2Lx/3, ends on the x-faces
+    px = np.array([0.0, Lx / 3, 2 * Lx / 3, Lx])
+    py = rng.uniform(0.25, 0.75, 4) * Ly
+    dist = np.full(x.shape, np.inf)
+    for i in range(3):
+        a = np.array([px[i], py[i]])
+        d = np.array([px[i + 1] - px[i], py[i + 1] - py[i]])
+        t = np.clip(((x - a[0]) * d[0] + (y - a[1]) * d[1]) / (d @ d), 0.0, 1.0)
+        dist = np.minimum(dist, np.hypot(x - a[0] - t * d[0], y - a[1] - t * d[1]))
+    c2 = np.where(dist < 0.5 * width, c_frac, c2)
+    return np.broadcast_to(c2, (nz, ny, nx)).copy()
+
+
 def smooth_random_field(shape, rng, corr=4.0):
     """Zero-mean, unit-std Gaussian random field with Gaussian correlation
     length ``corr`` cells (FFT filtering of white noise)."""
@@ -365,6 +395,32 @@ def config5(seed=SEED):
     return Problem("cfg5_512x512x256_32c_128shots", nx, ny, nz, h, c, xc, yc, zc,
                    np.full(2048, 8), np.full(2048, 24), default_sigma(20.0, 8.0), 20.0,
                    src, rec, 6000)
+
+
+def paper_layout(seed=SEED, cells_per_unit=20, m=25, k=3):
+    """Stand-in for the paper's experiment (section "Numerical experiments"),
+    in its dimensionless units: the box [0,7] x [0,7] x [0,3] split into
+    7 x 7 x 3 unit cubes of ``cells_per_unit``^3 cells, m = 25 face modes
+    (5 x 5), k = n = 3 levels, c(x, y) from ``skew_fracture`` (its model is
+    shown only in a figure), one source at (3.5, 1.5, 1.5) whose Ricker band
+    edge (2.5 f_peak) gives a shortest wavelength of 0.78 at c = 1, traces
+    u(x, 0, 1.5) at every node x of the line, t in [0, 12.5].  The outer
+    faces are homogeneous Neumann (the paper's absorbing conditions are not
+    built).  The Krylov shift is small, sigma = (2 pi 0.1 f_peak)^2: the
+    paper's subspace uses sigma = 0, which a subdomain with Neumann faces
+    does not allow.  ``nsteps`` is left for the caller: it follows from the
+    time step of the run."""
+    h = 1.0 / cells_per_unit
+    nx, ny, nz = 7 * cells_per_unit, 7 * cells_per_unit, 3 * cells_per_unit
+    rng = np.random.default_rng(seed)
+    c = skew_fracture(nx, ny, nz, h, rng)
+    cuts = [uniform_cuts(n, cells_per_unit) for n in (nx, ny, nz)]
+    nsub = 7 * 7 * 3
+    f_peak = 1.0 / (2.5 * 0.78)
+    rec = np.stack([np.arange(nx + 1) * h, np.zeros(nx + 1), np.full(nx + 1, 1.5)], axis=1)
+    return Problem(f"paper_7x7x3_unit_cubes_m{m}_k{k}", nx, ny, nz, h, c, cuts[0], cuts[1],
+                   cuts[2], np.full(nsub, m), np.full(nsub, k), default_sigma(f_peak, 0.1), f_peak,
+                   np.array([[3.5, 1.5, 1.5]]), rec, 0, meta={"t_end": 12.5})
 
 
 def small_problem(ncell=(8, 8, 8), cuts=(4, 4, 4), m=4, k=3, h=10.0, seed=SEED,
