@@ -86,6 +86,17 @@ int bfail(sfm_handle* h, int code, const std::string& msg) {
                                                 std::to_string((int)s__));            \
     } while (0)
 
+// Frees the device temporaries it names when it leaves scope, so that an
+// error return does not leak them (those already freed are null).
+template <typename... P>
+struct DevGuard {
+    std::tuple<P*&...> ptrs;
+    explicit DevGuard(P*&... p) : ptrs(p...) {}
+    ~DevGuard() { std::apply([](auto&... q) { (dfree(q), ...); }, ptrs); }
+    DevGuard(const DevGuard&) = delete;
+    DevGuard& operator=(const DevGuard&) = delete;
+};
+
 template <typename P>
 cudaError_t dmalloc(P*& p, size_t count) {
     dfree(p);
@@ -302,6 +313,7 @@ extern "C" int sfm_build_roms(sfm_handle* h, const int* m_sub, const int* k_sub,
 
     int* d_err = nullptr;
     double* d_ratio = nullptr;
+    DevGuard guard_top(d_coef, d_err, d_ratio);
     BCK(h, dmalloc(d_err, 1));
     BCK(h, cudaMemsetAsync(d_err, 0, sizeof(int), st));
     int cg_iters_max = 0;
@@ -332,6 +344,7 @@ extern "C" int sfm_build_roms(sfm_handle* h, const int* m_sub, const int* k_sub,
         }
         ColSpec* d_cs = nullptr;
         double* Bm = nullptr;
+        DevGuard guard_basis(d_cs, Bm);
         BCK(h, dmalloc(d_cs, cs.size()));
         BCK(h, cudaMemcpyAsync(d_cs, cs.data(), cs.size() * sizeof(ColSpec), cudaMemcpyHostToDevice, st));
         BCK(h, dmalloc(Bm, (size_t)N * b));
@@ -342,6 +355,7 @@ extern "C" int sfm_build_roms(sfm_handle* h, const int* m_sub, const int* k_sub,
         const long long sV = (long long)N * n;
         double *tmp = nullptr, *Gm = nullptr, *R1 = nullptr, *R1i = nullptr, *R2 = nullptr,
                *R2i = nullptr, *Rr = nullptr;
+        DevGuard guard_work(tmp, Gm, R1, R1i, R2, R2i, Rr);
         BCK(h, dmalloc(c.V, (size_t)S * sV));
         BCK(h, dmalloc(tmp, (size_t)S * N * b));
         BCK(h, dmalloc(Gm, (size_t)S * n * b));
@@ -362,6 +376,7 @@ extern "C" int sfm_build_roms(sfm_handle* h, const int* m_sub, const int* k_sub,
         double *Xc = nullptr, *Rc = nullptr, *Zc = nullptr, *Pc = nullptr, *Qc = nullptr,
                *rhs = nullptr, *rz = nullptr, *rz2 = nullptr, *pq = nullptr, *rr = nullptr,
                *rr0 = nullptr;
+        DevGuard guard_cg(Xc, Rc, Zc, Pc, Qc, rhs, rz, rz2, pq, rr, rr0);
         const size_t ncolv = (size_t)S * b;
         if (k > 1) {
             for (double** p : {&Xc, &Rc, &Zc, &Pc, &Qc, &rhs}) BCK(h, dmalloc(*p, ncolv * N));
@@ -421,12 +436,14 @@ extern "C" int sfm_build_roms(sfm_handle* h, const int* m_sub, const int* k_sub,
         for (double** p : {&Xc, &Rc, &Zc, &Pc, &rhs, &rz, &rz2, &pq, &rr, &rr0}) dfree(*p);
         // Galerkin ROM  L~ = V^T L V (column chunks), F~ = V^T F
         double *Lt = nullptr, *Ft = nullptr, *LVc = nullptr;
+        DevGuard guard_rom(Lt, Ft, LVc);
         int chunk = std::min(n, 96);
         while (n % chunk) --chunk;                       // equal column chunks
         BCK(h, dmalloc(Lt, (size_t)S * n * n));
         BCK(h, dmalloc(Ft, (size_t)S * n * b));
         BCK(h, dmalloc(LVc, (size_t)S * N * chunk));
         double* Vcol = nullptr;
+        DevGuard guard_vcol(Vcol);
         BCK(h, dmalloc(Vcol, (size_t)S * N * chunk));
         for (int c0 = 0; c0 < n; c0 += chunk) {
             const int w = std::min(chunk, n - c0);
@@ -450,6 +467,7 @@ extern "C" int sfm_build_roms(sfm_handle* h, const int* m_sub, const int* k_sub,
         dfree(d_cs);
         // block Lanczos on (L~, F~) with full reorthogonalisation
         double *al = nullptr, *Cm = nullptr, *Rl = nullptr, *Wl = nullptr, *tl = nullptr;
+        DevGuard guard_lanczos(al, Cm, Rl, Wl, tl);
         BCK(h, dmalloc(c.Qh, (size_t)S * n * n));
         BCK(h, dmalloc(al, (size_t)S * k * bb));
         BCK(h, dmalloc(Cm, (size_t)S * std::max(1, k - 1) * bb));   // level-major [k-1][S]
@@ -490,6 +508,7 @@ extern "C" int sfm_build_roms(sfm_handle* h, const int* m_sub, const int* k_sub,
         dfree(Lt); dfree(Ft); dfree(Wl); dfree(tl);
         // S-fraction transform
         double *Gam = nullptr, *Gh = nullptr;
+        DevGuard guard_gamma(Gam, Gh);
         BCK(h, dmalloc(Gam, (size_t)S * k * bb));
         BCK(h, dmalloc(Gh, (size_t)S * k * bb));
         BCK(h, dmalloc(c.Ginv, (size_t)S * k * bb));
@@ -524,6 +543,7 @@ extern "C" int sfm_build_roms(sfm_handle* h, const int* m_sub, const int* k_sub,
     int nreg = 0;
     {
         int* d_nreg = nullptr;
+        DevGuard guard_nreg(d_nreg);
         BCK(h, dmalloc(d_nreg, 1));
         BCK(h, cudaMemsetAsync(d_nreg, 0, sizeof(int), st));
         BCK(h, cudaFuncSetAttribute(sfm::psd_project_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -673,6 +693,7 @@ static int project_points(sfm_handle* h, int npts, const double* xyz, int kind, 
         }
         int *d_psub = nullptr, *d_nptr = nullptr, *d_nodes = nullptr;
         double *d_w = nullptr, *Y = nullptr, *Z = nullptr, *R = nullptr;
+        DevGuard guard_points(d_psub, d_nptr, d_nodes, d_w, Y, Z, R);
         BCK(h, dmalloc(d_psub, np));
         BCK(h, dmalloc(d_nptr, np + 1));
         BCK(h, dmalloc(d_nodes, nodes.size()));

@@ -289,10 +289,11 @@ static int set_coeffs_common(sfm_handle* h, const double* coeffs, bool on_device
     for (int s = 0; s < h->nsub; ++s)
         gh1[s] = h->coef_off[s] + (long long)h->k[s] * h->b[s] * h->b[s];
     long long* d_gh1 = nullptr;
-    CK(h, upload(d_gh1, gh1.data(), gh1.size(), st));
-    CK(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
-    cudaError_t e = sfm::launch_face_H(h->d_coef64, d_gh1, h->d_b, h->d_face_off, h->d_nbr,
-                                       h->d_H_off, h->d_H64, h->nsub, h->d_err, st);
+    cudaError_t e = upload(d_gh1, gh1.data(), gh1.size(), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(int), st);
+    if (e == cudaSuccess)
+        e = sfm::launch_face_H(h->d_coef64, d_gh1, h->d_b, h->d_face_off, h->d_nbr, h->d_H_off,
+                               h->d_H64, h->nsub, h->d_err, st);
     int herr = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
