@@ -123,18 +123,27 @@ def cfl_dt(K, mass):
     return 2.0 / np.sqrt(lambda_max(K, mass))
 
 
-def leapfrog(K, mass, dt, nsteps, force, wavelet, rec_rows):
+def leapfrog(K, mass, dt, nsteps, force, wavelet, rec_rows, u0=None, v0=None):
     """Fine-grid explicit leapfrog
     ``M (u^{n+1} - 2u^n + u^{n-1}) = dt^2 (-K u^n + force * f(t_n))`` from rest,
     in increment form ``v^{n+1} = v^n + dt^2 M^{-1}(...)``, ``u^{n+1} = u^n + v^{n+1}``.
 
     ``force``: [N] nodal force density; ``wavelet``: samples f(t_n), n < nsteps;
     ``rec_rows``: sparse [nrec, N].  Returns traces ``[nrec, nsteps+1]`` at
-    ``t_n = n dt``."""
+    ``t_n = n dt``.
+
+    ``u0``, ``v0``: optional initial displacement and velocity [N]; the start
+    is the second-order Taylor step of the ROM stepping,
+    ``v^0 = dt v0 - dt^2/2 M^{-1}(-K u0)``, so that
+    ``u^1 = u0 + dt v0 + dt^2/2 M^{-1}(-K u0) + dt^2 M^{-1} force f(t_0)``."""
     n = K.shape[0]
-    u = np.zeros(n)
-    v = np.zeros(n)
     minv = 1.0 / mass
+    u = np.zeros(n) if u0 is None else np.array(u0, dtype=np.float64)
+    v = np.zeros(n)
+    if u0 is not None:
+        v -= 0.5 * dt * dt * minv * (-(K @ u))
+    if v0 is not None:
+        v += dt * np.asarray(v0, dtype=np.float64)
     out = np.zeros((rec_rows.shape[0], nsteps + 1))
     for it in range(nsteps):
         out[:, it] = rec_rows @ u

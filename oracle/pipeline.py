@@ -171,15 +171,40 @@ def slit_system(problem):
     subdomain operators ``K^a, M^a`` assembled with only the OPEN-face nodes
     of shared faces identified; subdomain edge and corner nodes keep one copy
     per subdomain.  Returns ``(K, M, force, rec_rows)``."""
+    pieces, n = slit_nodes(problem)
+    Kg = sp.csr_matrix((n, n))
+    Mg = np.zeros(n)
+    for box, gidx in pieces:
+        K, m = fine.assemble(problem.c, problem.h, box)
+        P = sp.csr_matrix((np.ones(len(gidx)), (gidx, np.arange(len(gidx)))), shape=(n, len(gidx)))
+        Kg = Kg + P @ K @ P.T
+        np.add.at(Mg, gidx, m)
+    return (Kg.tocsr(), Mg) + _point_vectors(problem, None, pieces, n)
+
+
+def slit_field(problem, field):
+    """A nodal field [nz+1, ny+1, nx+1] on the slit grid's unknowns (every
+    copy of a node takes the node's value)."""
+    pieces, n = slit_nodes(problem)
+    out = np.zeros(n)
+    f = np.asarray(field, dtype=np.float64)
+    for box, gidx in pieces:
+        x0, x1, y0, y1, z0, z1 = box
+        out[gidx] = f[z0:z1 + 1, y0:y1 + 1, x0:x1 + 1].ravel()
+    return out
+
+
+def slit_nodes(problem):
+    """Numbering of the slit grid: per subdomain ``(box, gidx)``, the slit
+    unknown of each local node; open-face nodes of shared faces are numbered
+    once, every other node once per subdomain.  Returns ``(pieces, n)``."""
     topo = faces.Topology(problem)
     gid_of = {}
     pieces = []
     nxt = 0
-    Ks, Ms = [], []
     for s in range(problem.nsub):
         box = problem.sub_box(s)
-        K, m = fine.assemble(problem.c, problem.h, box)
-        gidx = -np.ones(K.shape[0], dtype=int)
+        gidx = -np.ones(int(np.prod(fine.box_shape(box))), dtype=int)
         for f in range(6):
             if topo.nbr[s, f] < 0:
                 continue
@@ -195,24 +220,16 @@ def slit_system(problem):
         gidx[free] = nxt + np.arange(free.sum())
         nxt += int(free.sum())
         pieces.append((box, gidx))
-        Ks.append(K)
-        Ms.append(m)
-    n = nxt
-    Kg = sp.csr_matrix((n, n))
-    Mg = np.zeros(n)
-    for (box, gidx), K, m in zip(pieces, Ks, Ms):
-        P = sp.csr_matrix((np.ones(len(gidx)), (gidx, np.arange(len(gidx)))), shape=(n, len(gidx)))
-        Kg = Kg + P @ K @ P.T
-        np.add.at(Mg, gidx, m)
-    return (Kg.tocsr(), Mg) + _point_vectors(problem, None, pieces, n)
+    return pieces, nxt
 
 
-def fine_traces(system, dt, nsteps, wavelet):
+def fine_traces(system, dt, nsteps, wavelet, u0=None, v0=None):
     """Fine-grid leapfrog traces ``[nshots, nrec, nsteps+1]`` of a system from
-    :func:`fine_system` / :func:`slit_system`."""
+    :func:`fine_system` / :func:`slit_system`; ``u0``, ``v0``: optional
+    initial fields in the system's own unknowns, shared by every shot."""
     K, mass, force, R = system
     wavelet = np.asarray(wavelet).reshape(force.shape[1], -1)
-    return np.stack([fine.leapfrog(K, mass, dt, nsteps, force[:, q], wavelet[q], R)
+    return np.stack([fine.leapfrog(K, mass, dt, nsteps, force[:, q], wavelet[q], R, u0, v0)
                      for q in range(force.shape[1])])
 
 

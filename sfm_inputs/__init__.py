@@ -423,6 +423,20 @@ def paper_layout(seed=SEED, cells_per_unit=20, m=25, k=3):
                    np.array([[3.5, 1.5, 1.5]]), rec, 0, meta={"t_end": 12.5})
 
 
+def gaussian_pulse(problem: Problem, xyz, width):
+    """Initial displacement ``exp(-r^2 / 2 width^2)`` around ``xyz`` on the
+    grid nodes, ``[nz+1, ny+1, nx+1]`` (the initial-value form of a source:
+    Algorithm 1 starts from initial conditions).  For the paper layout a
+    width of ``3 * 0.78 / (2 pi)`` puts the spectrum's 1% point at the
+    shortest wavelength 0.78."""
+    h = problem.h
+    k, j, i = np.meshgrid(np.arange(problem.nz + 1), np.arange(problem.ny + 1),
+                          np.arange(problem.nx + 1), indexing="ij")
+    x = np.asarray(xyz, dtype=np.float64)
+    r2 = (i * h - x[0]) ** 2 + (j * h - x[1]) ** 2 + (k * h - x[2]) ** 2
+    return np.exp(-r2 / (2.0 * width * width))
+
+
 def small_problem(ncell=(8, 8, 8), cuts=(4, 4, 4), m=4, k=3, h=10.0, seed=SEED,
                   model="layers", f_peak=None, nsteps=200, src=None, rec=None,
                   m_sub=None, k_sub=None, sigma=None):

@@ -158,3 +158,45 @@ def test_shared_face_basis_agrees_on_both_sides():
             kb = [(gb[0][q], gb[1][q], gb[2][q]) for q in ib]
             assert ka == kb
             assert np.array_equal(va, vb)
+
+
+def test_fine_initial_value_start_follows_the_discrete_cosine_and_sine():
+    """The fine leapfrog's initial-value start: for an eigenvector phi of
+    M^{-1} K (K phi = lam M phi), u0 = phi gives u^n = phi cos(n th) with
+    2 (1 - cos th) = dt^2 lam, and v0 = phi gives dt phi sin(n th) / sin th."""
+    p = inputs.small_problem(ncell=(5, 4, 3), cuts=(5, 4, 3), model="random")
+    K, mass = fine.assemble(p.c, p.h, fine.global_box(p))
+    s = 1.0 / np.sqrt(mass)
+    lam_all, Y = np.linalg.eigh((s[:, None] * K.toarray()) * s[None, :])
+    dt = 0.9 * 2.0 / np.sqrt(lam_all[-1])
+    nsteps = 300
+    R = sp.identity(K.shape[0], format="csr")[::7]
+    zero = np.zeros(K.shape[0])
+    n = np.arange(nsteps + 1)
+    for idx in (1, K.shape[0] // 2, K.shape[0] - 2):
+        phi = s * Y[:, idx]
+        th = np.arccos(1.0 - 0.5 * dt * dt * lam_all[idx])
+        got = fine.leapfrog(K, mass, dt, nsteps, zero, np.zeros(nsteps), R, u0=phi)
+        ref = (R @ phi)[:, None] * np.cos(n * th)[None, :]
+        assert pipeline.rel_l2(got, ref) < 1e-9, idx
+        got = fine.leapfrog(K, mass, dt, nsteps, zero, np.zeros(nsteps), R, v0=phi)
+        ref = dt * (R @ phi)[:, None] * (np.sin(n * th) / np.sin(th))[None, :]
+        assert pipeline.rel_l2(got, ref) < 1e-9, idx
+
+
+def test_slit_field_copies_every_node_value():
+    """Every slit unknown of a node carries the node's value, and a field
+    that is constant stays constant; the slit grid has one extra copy per
+    extra subdomain sharing an edge or corner node."""
+    p = inputs.small_problem(ncell=(8, 8, 8), cuts=(4, 4, 4), model="random")
+    pieces, n = pipeline.slit_nodes(p)
+    rng = np.random.default_rng(5)
+    field = rng.standard_normal((p.nz + 1, p.ny + 1, p.nx + 1))
+    u = pipeline.slit_field(p, field)
+    for box, gidx in pieces:
+        i, j, k = fine.node_coords(box)
+        np.testing.assert_array_equal(u[gidx], field[k, j, i])
+    assert np.all(pipeline.slit_field(p, np.ones_like(field)) == 1.0)
+    K, mass, _, _ = pipeline.slit_system(p)
+    assert K.shape == (n, n) and n > (p.nx + 1) * (p.ny + 1) * (p.nz + 1)
+    assert abs(mass.sum() - fine.global_mass_ijk(p).sum()) < 1e-9 * mass.sum()

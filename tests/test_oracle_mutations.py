@@ -78,3 +78,13 @@ def test_arithmetic_instead_of_harmonic_face_coupling_is_caught(monkeypatch):
     monkeypatch.setattr(coupled, "face_H", bad)
     with pytest.raises(AssertionError):
         coupled_pins.test_rom_converges_to_the_slit_fine_grid()
+
+
+def test_wrong_sign_of_the_fine_half_step_start_is_caught(monkeypatch):
+    import test_oracle_fine as fine_pins
+    from oracle import fine
+    fine_pins.test_fine_initial_value_start_follows_the_discrete_cosine_and_sine()
+    bad = _mutant(fine, "leapfrog", "v -= 0.5 * dt * dt * minv", "v += 0.5 * dt * dt * minv")
+    monkeypatch.setattr(fine, "leapfrog", bad)
+    with pytest.raises(AssertionError):
+        fine_pins.test_fine_initial_value_start_follows_the_discrete_cosine_and_sine()
