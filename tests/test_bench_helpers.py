@@ -1,0 +1,48 @@
+"""The byte counts behind bench.py's roofline, checked on the CPU against
+independent counts: the oracle's face topology and a direct count of the
+(receiver, subdomain) pairs."""
+import numpy as np
+
+import sfm_inputs as inputs
+from oracle import faces
+
+
+def _pairs(p):
+    """(receiver, subdomain) pairs: a subdomain's closed node box holds a
+    node with nonzero trilinear weight of the receiver."""
+    out = 0
+    boxes = np.array([p.sub_box(s) for s in range(p.nsub)])
+    for x in p.rec_xyz:
+        nodes, _ = inputs.trilinear_node_weights(x, p.h, p.nx, p.ny, p.nz)
+        hit = np.zeros(p.nsub, dtype=bool)
+        for i, j, k in nodes:
+            hit |= ((boxes[:, 0] <= i) & (i <= boxes[:, 1]) & (boxes[:, 2] <= j) & (j <= boxes[:, 3])
+                    & (boxes[:, 4] <= k) & (k <= boxes[:, 5]))
+        out += int(hit.sum())
+    return out
+
+
+def test_face_modes_match_the_oracle_topology():
+    import bench
+    for p in (inputs.config3(), inputs.small_problem(ncell=(12, 8, 8), cuts=(4, 4, 8),
+                                                      m_sub=[3, 5, 4, 6, 2, 7])):
+        np.testing.assert_array_equal(bench.face_modes(p), faces.Topology(p).mf)
+
+
+def test_config2_bytes_per_step():
+    """Config 2 (512 subdomains, b = 48, k = 16, m = 8, one shot): packed
+    coefficients (2k - 1) b(b+1)/2 per subdomain, six m(m+1)/2 face blocks,
+    k b numbers per receiver pair, and per shot U and delta read and written
+    plus the face data written and read back."""
+    import bench
+    p = inputs.config2()
+    npairs = _pairs(p)
+    assert npairs == 2196          # 1024 receivers on the y = 96h cut plane
+    rec = bench.receiver_row_numbers(p)
+    assert rec == npairs * 16 * 48
+    per_sub = 31 * 48 * 49 // 2 + 6 * 8 * 9 // 2 + 4 * 16 * 48 + 2 * 48
+    want = (512 * per_sub + rec) * 4
+    assert bench.algorithmic_bytes_per_step(p, 1, rec, 4) == want == 88338432
+    assert bench.algorithmic_bytes_per_step(p, 1, rec, 8) == 2 * want
+    # more shots add only the per-shot state
+    assert (bench.algorithmic_bytes_per_step(p, 3, rec, 4) - want) == 2 * 512 * (4 * 16 * 48 + 2 * 48) * 4
