@@ -16,7 +16,7 @@ Pieces, in the order the data flows:
   S-fraction (Eqs. 12-13) whatever the network outputs;
 * level 1 from its closed forms, Gammahat_1 = F^T F and
   Gamma_1 = Gammahat_1^{-1} F^T L F Gammahat_1^{-1} (no solves);
-* judged by the NtD map S(lambda) = F^T (L + lambda)^{-1} F, the transfer
+* measured by the NtD map S(lambda) = F^T (L + lambda)^{-1} F, the transfer
   function of the S-fraction (Eq. 15), at complex lambda = (eta + i w)^2;
 * fallback: the block solve F^T (L + sigma)^{-1} F at one shift against the
   decoded S(sigma); above the tolerance the exact build is used.
