@@ -273,6 +273,42 @@ int sfm_project_receivers(sfm_handle* h, int nrec, const double* xyz);
 int sfm_free_build(sfm_handle* h);
 
 /*
+ * Usable depth of each subdomain's S-fraction (an extension of the offline
+ * stage; the paper's ROMs are three levels deep).  Deep levels of an
+ * accurate ROM at a small shift run past FP64's dynamic range: their
+ * Gamma_j, Gammahat_j (Eq. 13) have eigenvalues at the rounding level and
+ * the fraction's stability limit falls far below the Galerkin ROM's.  The
+ * usable depth of subdomain s is the number of leading levels before the
+ * first level j whose Gammahat_j, or Gamma_j for j < k_s (Gamma_k is
+ * semidefinite by construction), has lambda_min <= tau * lambda_max; at
+ * least one level is kept.
+ *
+ * sfm_usable_depths is the decision alone, on the host (no device work):
+ *   range[nsub][2*kmax][2]  (lambda_min, lambda_max) of the blocks of each
+ *                           subdomain in the sfm_set_coeffs order (Gamma_1..k
+ *                           then Gammahat_1..k); entries past 2 k_s unused
+ *   depth[nsub]             out
+ * Errors: SFM_ERR_ARG (tau outside [0, 1), k_s outside 1..kmax).
+ *
+ * sfm_cut_depth computes the ranges of the coefficients held (FP64 cyclic
+ * Jacobi on the device), decides the depths with sfm_usable_depths and,
+ * when a level goes, keeps levels 1..d_s of every subdomain: coefficients,
+ * source, receiver and initial rows (their first d_s levels), set again as
+ * sfm_set_topology, sfm_set_coeffs, sfm_set_sources, sfm_set_receivers and
+ * sfm_set_initial would; the cut fraction is terminated with U_{d+1} = 0
+ * like the full one (Eq. 12).  It releases the offline bases as
+ * sfm_free_build does (they describe the uncut fraction), so project the
+ * sources and receivers first.  depth_out (depth_cap >= nsub entries, the
+ * kept depths) and nlevels_cut (levels removed in all) may be NULL.
+ * Errors: SFM_ERR_ARG, SFM_ERR_STATE (no
+ * coefficients), SFM_ERR_CUDA, SFM_ERR_NOMEM; after an error past the
+ * decision the handle's ROM data are undefined and must be set again.
+ */
+int sfm_usable_depths(int nsub, const int* k_sub, int kmax, const double* range, double tau,
+                      int* depth);
+int sfm_cut_depth(sfm_handle* h, double tau, int* depth_out, int depth_cap, int* nlevels_cut);
+
+/*
  * sfm_run_static - the FP64 coupled stepping of sfm_run without allocating
  * any device memory.  (Not a step of the paper's method, which has no
  * counterpart to it: it serves callers of this library that cannot allocate

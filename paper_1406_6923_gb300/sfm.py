@@ -36,7 +36,8 @@ EXPORTS = ["sfm_create", "sfm_destroy", "sfm_last_error", "sfm_set_stream", "sfm
            "sfm_set_coeffs", "sfm_get_coeffs", "sfm_set_sources", "sfm_set_receivers",
            "sfm_run", "sfm_cfl_dt", "sfm_last_launches", "sfm_debug_set", "sfm_set_model",
            "sfm_build_roms", "sfm_project_sources", "sfm_project_receivers", "sfm_free_build", "sfm_run_static",
-           "sfm_autotune", "sfm_set_initial", "sfm_plan_pieces"]
+           "sfm_autotune", "sfm_set_initial", "sfm_plan_pieces", "sfm_usable_depths",
+           "sfm_cut_depth"]
 
 
 class sfm_build_report(C.Structure):
@@ -92,6 +93,8 @@ def load(path=LIB_PATH):
         "sfm_autotune": (_i, [_p, _i, _i, _ip, _ip, _dp]),
         "sfm_set_initial": (_i, [_p, _i, _i, _ip, _ip, _dp, _dp]),
         "sfm_plan_pieces": (_i, [_i, _i, _ip, _i, _ip, _ip, _i, _ip]),
+        "sfm_usable_depths": (_i, [_i, _ip, _i, _dp, C.c_double, _ip]),
+        "sfm_cut_depth": (_i, [_p, C.c_double, _ip, _i, _ip]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -273,6 +276,27 @@ def sfm_project_receivers(h, xyz):
 
 def sfm_free_build(h):
     _check(h, load().sfm_free_build(h))
+
+
+def sfm_usable_depths(k_sub, range_, tau=1e-13):
+    """Depth decision alone (host): ``range_`` [nsub][2*kmax][2] of
+    (lambda_min, lambda_max) per block, kmax = range_.shape[1] // 2."""
+    k, kp = _iarr(k_sub)
+    r, rp = _darr(np.asarray(range_).reshape(len(k), -1, 2))
+    depth = np.zeros(len(k), dtype=np.int32)
+    _check(None, load().sfm_usable_depths(len(k), kp, r.shape[1] // 2, rp, float(tau),
+                                          depth.ctypes.data_as(_ip)))
+    return depth
+
+
+def sfm_cut_depth(h, nsub, tau=1e-13):
+    """Cut every subdomain's fraction to its usable depth; returns (depths,
+    levels removed)."""
+    depth = np.zeros(int(nsub), dtype=np.int32)
+    n = C.c_int(0)
+    _check(h, load().sfm_cut_depth(h, float(tau), depth.ctypes.data_as(_ip), len(depth),
+                                   C.byref(n)))
+    return depth, n.value
 
 
 def sfm_run_static(device, stream_ptr, k_sub, m_face, nbr, coeffs_ptr, nshots, src_shot, src_sub,
