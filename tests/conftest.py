@@ -9,3 +9,5 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (run with -m gpu)")
     config.addinivalue_line("markers", "slow: takes more than a few seconds on the CPU")
+    config.addinivalue_line("markers", "gpu_pending: needs a CUDA GPU and has not run on one "
+                                       "yet (run with -m gpu_pending; skipped without a GPU)")
