@@ -81,6 +81,9 @@ def main(argv=None):
     ap.add_argument("--k", type=int, default=3)
     ap.add_argument("--sigma-factor", type=float, default=None,
                     help="shift (2 pi factor f_peak)^2 instead of the layout's")
+    ap.add_argument("--shift-factors", default=None,
+                    help="comma-separated factors f_j of distinct shifts (2 pi f_j f_peak)^2, "
+                         "one per block after the first (Eq. 6)")
     ap.add_argument("--source-x", type=float, default=None)
     ap.add_argument("--start", choices=("source", "pulse"), default="source",
                     help="a Ricker point source from rest, or a Gaussian initial pulse "
@@ -89,13 +92,16 @@ def main(argv=None):
     p = inputs.paper_layout(cells_per_unit=a.cells_per_unit, m=a.m, k=a.k)
     if a.sigma_factor is not None:
         p.sigma = inputs.default_sigma(p.f_peak, a.sigma_factor)
+    if a.shift_factors:
+        p.sigma = [inputs.default_sigma(p.f_peak, float(f)) for f in a.shift_factors.split(",")]
     if a.source_x is not None:
         p.src_xyz[0, 0] = a.source_x
     u0 = None
     if a.start == "pulse":
         u0 = inputs.gaussian_pulse(p, p.src_xyz[0], 3.0 * 0.78 / (2.0 * np.pi))
     out = {"workload": p.name, "cells_per_unit": a.cells_per_unit, "m": a.m, "k": a.k,
-           "sigma": p.sigma, "source": p.src_xyz[0].tolist(), "start": a.start}
+           "sigma": p.sigma if np.ndim(p.sigma) else float(p.sigma),
+           "source": p.src_xyz[0].tolist(), "start": a.start}
     out.update(trace_errors(p, p.meta["t_end"], u0))
     print(json.dumps(out))
 

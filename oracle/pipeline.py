@@ -21,7 +21,16 @@ class SubdomainROM:
         self.F = self.B / np.sqrt(self.mass)[:, None]
         self.sigma = problem.sigma
         self.k = int(problem.k_sub[s])
-        solve = rom.shifted_solver(self.K, self.mass, self.sigma)
+        if np.ndim(self.sigma) == 0:
+            solve = rom.shifted_solver(self.K, self.mass, self.sigma)
+        else:
+            # distinct shifts (Eq. 6): one per block after F, the first k-1
+            # of the problem's list
+            shifts = [float(x) for x in self.sigma[:self.k - 1]]
+            if len(shifts) < self.k - 1:
+                raise ValueError("fewer shifts than blocks after the first")
+            cache = {x: rom.shifted_solver(self.K, self.mass, x) for x in set(shifts)}
+            solve = [cache[x] for x in shifts]
         V = rom.krylov_basis(solve, self.F, self.k)
         L = fine.symmetrised(self.K, self.mass)
         self.Lt, self.Ft = rom.galerkin(L, V, self.F)

@@ -17,6 +17,11 @@ Cholesky factor of the SPD matrix ``K + sigma M``.
 Block Gram-Schmidt against all previous blocks is done twice (full
 reorthogonalisation); a numerically rank-deficient new block raises
 ``Breakdown`` (deflation would make the Lanczos blocks rectangular).
+
+Eq. 6 also allows distinct finite shifts sigma_1..sigma_{k-1}: block j+1 is
+then ``(L + sigma_j)^{-1}`` applied to block j, which for distinct shifts
+spans ``F, (L+sigma_1)^{-1}F, ..., (L+sigma_{k-1})^{-1}F`` (partial
+fractions) and for repeated ones the powers above.
 """
 from __future__ import annotations
 
@@ -53,11 +58,16 @@ def _qr(W, tol, what):
 
 
 def krylov_basis(solve, F, k, tol=1e-12):
-    """Orthonormal ``V = [Q_1 .. Q_k]`` of the shifted block Krylov space."""
+    """Orthonormal ``V = [Q_1 .. Q_k]`` of the shifted block Krylov space.
+    ``solve``: one resolvent ``x -> (L + sigma)^{-1} x`` for every block, or
+    a list of k-1 of them, the j-th making block j+1."""
+    solves = list(solve) if isinstance(solve, (list, tuple)) else [solve] * (k - 1)
+    if len(solves) != k - 1:
+        raise ValueError("one resolvent per block after the first")
     Q, _ = _qr(F, tol, "F")
     blocks = [Q]
-    for _ in range(1, k):
-        W = solve(blocks[-1])
+    for j in range(1, k):
+        W = solves[j - 1](blocks[-1])
         for _ in range(2):
             for Qi in blocks:
                 W = W - Qi @ (Qi.T @ W)

@@ -88,3 +88,17 @@ def test_wrong_sign_of_the_fine_half_step_start_is_caught(monkeypatch):
     monkeypatch.setattr(fine, "leapfrog", bad)
     with pytest.raises(AssertionError):
         fine_pins.test_fine_initial_value_start_follows_the_discrete_cosine_and_sine()
+
+
+def test_one_shift_for_every_block_is_caught(monkeypatch):
+    """Distinct shifts (Eq. 6) collapsed to the first one: the ROM no longer
+    interpolates the NtD map at the other shifts."""
+    import test_oracle_multishift as ms_pins
+    from oracle import pipeline
+    ms_pins.test_interpolates_the_ntd_map_and_its_derivative_at_every_shift(ms_pins.multi.__wrapped__())
+    bad = _mutant(pipeline, "SubdomainROM", "solve = [cache[x] for x in shifts]",
+                  "solve = [cache[shifts[0]] for x in shifts]")
+    monkeypatch.setattr(pipeline, "SubdomainROM", bad)
+    with pytest.raises(AssertionError):
+        ms_pins.test_interpolates_the_ntd_map_and_its_derivative_at_every_shift(
+            ms_pins.multi.__wrapped__())
