@@ -84,3 +84,8 @@ def test_bad_arguments_are_rejected():
         sfm.sfm_usable_depths([2], r, 1.5)
     with pytest.raises(sfm.SfmError):
         sfm.sfm_usable_depths([3], r, 1e-13)           # k above kmax = 2
+
+
+def test_cut_depth_rejects_a_null_handle_without_device_work():
+    lib = sfm.load()
+    assert lib.sfm_cut_depth(None, 1e-13, None, 0, None) == sfm.SFM_ERR_ARG
