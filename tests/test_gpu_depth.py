@@ -15,7 +15,7 @@ from rom_abi import load_into
 pytestmark = pytest.mark.gpu_pending
 
 TAU = 1e-13
-FP64_TOL = 1e-11
+FP64_TOL = 1e-9            # deep ROMs (k up to 24), as in the stepping tests
 
 
 @pytest.fixture(scope="module")
