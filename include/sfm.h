@@ -202,6 +202,31 @@ int sfm_autotune(sfm_handle* h, int precision, int nsteps, int* ncw, int* nstage
                  double* us_per_step);
 
 /*
+ * Checkpoint of the stepping state: U^N and the increment delta^N =
+ * U^N - U^{N-1} left by the last successful sfm_run (N its nsteps), for all
+ * its shots, converted to FP64, in a self-describing blob (native byte
+ * order, 8-byte aligned buffer): 8 int64 words {magic, version, nshots,
+ * nstate, nsub, topology fingerprint, N, precision} followed by U^N and
+ * delta^N, nshots * nstate doubles each, in the state layout (per shot,
+ * per subdomain, levels 1..k of b numbers).  *bytes: on entry the capacity
+ * of buf, on return the size needed; buf NULL only asks for the size.
+ * sfm_autotune and sfm_set_topology discard the state.  Errors:
+ * SFM_ERR_STATE (no state), SFM_ERR_ARG (capacity too small).
+ *
+ * Restore: the next sfm_run (and every later one, until sfm_set_initial or
+ * sfm_set_topology) starts from that U^0 and delta^0 instead of from rest,
+ * so an N-step run, its checkpoint, and an M-step run from the restored
+ * state with the wavelet samples N..N+M-1 give the traces of one N+M-step
+ * run (sample 0 of the second run repeats sample N of the first).  The
+ * handle's topology must match the checkpoint's and its source shot count
+ * must equal the checkpoint's at sfm_run.  Host buffer, copied.  Errors:
+ * SFM_ERR_ARG (not a checkpoint, other topology, size mismatch),
+ * SFM_ERR_STATE (no topology).
+ */
+int sfm_checkpoint(sfm_handle* h, void* buf, size_t* bytes);
+int sfm_restore(sfm_handle* h, const void* buf, size_t bytes);
+
+/*
  * ---------------------------------------------------------------------------
  * Offline stage on the GPU (Algorithm 1 stage 1, FP64)
  * ---------------------------------------------------------------------------

@@ -211,6 +211,7 @@ int sfm_cut_depth(sfm_handle* h, double tau, int* depth_out, int depth_cap, int*
         e = d2h(rrows.data(), h->d_rrows64, rrows.size() * sizeof(double));
     }
     const bool had_v0 = had_init && h->d_init_V64 != nullptr;
+    const bool had_delta = had_init && h->init_delta;    // a state from sfm_restore
     if (e == cudaSuccess && had_init) {
         U0.resize((size_t)h->init_nshots * h->nstate);
         e = d2h(U0.data(), h->d_init_U64, U0.size() * sizeof(double));
@@ -292,6 +293,7 @@ int sfm_cut_depth(sfm_handle* h, double tau, int* depth_out, int depth_cap, int*
                                           ini_sub.data(), U0_new.data(),
                                           had_v0 ? V0_new.data() : nullptr)) != SFM_OK)
         return rc;
+    h->init_delta = had_delta;      // a restored increment stays an increment
     return SFM_OK;
 }
 

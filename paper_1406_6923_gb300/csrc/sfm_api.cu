@@ -102,6 +102,9 @@ struct sfm_ext {
     int4* d_prec = nullptr;            // piece records (sfm::piece_records)
     int piece_grid = -1, piece_units = -1, piece_src = -1;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // state left by the last sfm_run (for sfm_checkpoint): its precision
+    // (-1: none), time steps and shot count
+    int ck_prec = -1, ck_steps = 0, ck_nshots = 0;
 };
 
 static sfm_ext* ext(sfm_handle* h) { return reinterpret_cast<sfm_ext*>(h->scratch); }
@@ -268,6 +271,7 @@ int sfm_set_topology(sfm_handle* h, int nsub, const int* k_sub, const int* m_fac
         CK(h, upload(h->d_frow, rows.data(), rows.size(), st));
     }
     h->have_coef = h->have_src = h->have_rec = h->have_init = false;
+    ext(h)->ck_prec = -1;
     invalidate(h);
     return SFM_OK;
 }
@@ -405,6 +409,7 @@ int sfm_set_initial(sfm_handle* h, int nshots, int npairs, const int* pair_shot,
     }
     h->init_nshots = nshots;
     h->have_init = true;
+    h->init_delta = false;
     return SFM_OK;
 }
 
@@ -712,7 +717,17 @@ static int run_impl(sfm_handle* h, double dt, int nsteps, const double* wavelet,
     for (int i = 0; i < 4; ++i) CK(h, cudaMemsetAsync(r.U[i], 0, nst * sizeof(T), st));
     CK(h, cudaMemsetAsync(r.rctr, 0, ((size_t)nsteps + 1) * sizeof(unsigned), st));
     CK(h, cudaMemsetAsync(r.dU, 0, nst * sizeof(T), st));
-    if (h->have_init) {
+    if (h->have_init && h->init_delta) {
+        // state restored by sfm_restore: U^0 and delta^0 themselves
+        if (h->init_nshots != h->nshots) {
+            dfree(tmp64);
+            return fail(h, SFM_ERR_STATE, "sfm_run: restored state has a different shot count");
+        }
+        cudaError_t e1 = sfm::launch_convert<P>(h->d_init_U64, r.U[0], nst, st);
+        if (e1 == cudaSuccess) e1 = sfm::launch_convert<P>(h->d_init_V64, r.dU, nst, st);
+        launches += 2;
+        if (e1 != cudaSuccess) { dfree(tmp64); return cuda_fail(h, e1, "restored state"); }
+    } else if (h->have_init) {
         // Algorithm 1 step 1.4: U^0 given, delta^0 = dt V^0 - dt^2/2 a_hom(U^0)
         // (the second-order Taylor start in increment form), computed in FP64
         if (h->init_nshots != h->nshots) {
@@ -802,15 +817,25 @@ extern "C" int sfm_run(sfm_handle* h, int precision, double dt, int nsteps, cons
     if (nsteps < 1 || !(dt > 0.0) || !wavelet || !traces)
         return fail(h, SFM_ERR_ARG, "sfm_run: bad arguments");
     CK(h, cudaSetDevice(h->device));
+    sfm_ext* x = ext(h);
+    x->ck_prec = -1;
+    int rc;
     if (precision == SFM_FP64)
-        return run_impl<sfm::PolF64>(h, dt, nsteps, wavelet, traces, flags, kernel_ms);
-    if (precision == SFM_FP32)
-        return run_impl<sfm::PolF32>(h, dt, nsteps, wavelet, traces, flags, kernel_ms);
-    if (precision == SFM_FP32X2)
-        return run_impl<sfm::PolF32x2>(h, dt, nsteps, wavelet, traces, flags, kernel_ms);
-    if (precision == SFM_FP32F)
-        return run_impl<sfm::PolF32F>(h, dt, nsteps, wavelet, traces, flags, kernel_ms);
-    return fail(h, SFM_ERR_ARG, "sfm_run: unknown precision");
+        rc = run_impl<sfm::PolF64>(h, dt, nsteps, wavelet, traces, flags, kernel_ms);
+    else if (precision == SFM_FP32)
+        rc = run_impl<sfm::PolF32>(h, dt, nsteps, wavelet, traces, flags, kernel_ms);
+    else if (precision == SFM_FP32X2)
+        rc = run_impl<sfm::PolF32x2>(h, dt, nsteps, wavelet, traces, flags, kernel_ms);
+    else if (precision == SFM_FP32F)
+        rc = run_impl<sfm::PolF32F>(h, dt, nsteps, wavelet, traces, flags, kernel_ms);
+    else
+        return fail(h, SFM_ERR_ARG, "sfm_run: unknown precision");
+    if (rc == SFM_OK) {
+        x->ck_prec = precision;
+        x->ck_steps = nsteps;
+        x->ck_nshots = h->nshots;
+    }
+    return rc;
 }
 
 // Shape search for the stepping kernel: every candidate (consumer warps,
@@ -862,6 +887,7 @@ extern "C" int sfm_autotune(sfm_handle* h, int precision, int nsteps, int* ncw, 
         return fail(h, SFM_ERR_STATE, "sfm_autotune: coefficients, sources and receivers must be set");
     if (nsteps < 1) return fail(h, SFM_ERR_ARG, "sfm_autotune: nsteps < 1");
     CK(h, cudaSetDevice(h->device));
+    ext(h)->ck_prec = -1;                  // the probes overwrite the run buffers
     if (precision == SFM_FP64) return autotune_impl<sfm::PolF64>(h, nsteps, ncw, nstage, us_per_step);
     if (precision == SFM_FP32) return autotune_impl<sfm::PolF32>(h, nsteps, ncw, nstage, us_per_step);
     if (precision == SFM_FP32X2)
@@ -869,6 +895,108 @@ extern "C" int sfm_autotune(sfm_handle* h, int precision, int nsteps, int* ncw, 
     if (precision == SFM_FP32F)
         return autotune_impl<sfm::PolF32F>(h, nsteps, ncw, nstage, us_per_step);
     return fail(h, SFM_ERR_ARG, "sfm_autotune: unknown precision");
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoint and restore of the stepping state.  Blob layout (native byte
+// order): 8 int64 header words {magic, version, nshots, nstate, nsub,
+// topology fingerprint, time steps behind the state, precision}, then U^N
+// and delta^N, nshots * nstate FP64 each, in the state layout.
+
+namespace {
+
+constexpr long long kCkMagic = 0x54504b434d4653LL;   // "SFMCKPT" little-endian
+constexpr long long kCkVersion = 1;
+
+long long topology_fingerprint(const sfm_handle* h) {
+    unsigned long long f = 1469598103934665603ull;     // FNV-1a over k, b, m, nbr
+    auto mix = [&](long long v) {
+        for (int i = 0; i < 8; ++i) {
+            f ^= (unsigned long long)((v >> (8 * i)) & 0xff);
+            f *= 1099511628211ull;
+        }
+    };
+    for (int s = 0; s < h->nsub; ++s) {
+        mix(h->k[s]);
+        mix(h->b[s]);
+        for (int q = 0; q < 6; ++q) {
+            mix(h->mface[s * 6 + q]);
+            mix(h->nbr[s * 6 + q]);
+        }
+    }
+    return (long long)(f >> 1);
+}
+
+double to_f64(double v) { return v; }
+double to_f64(float v) { return (double)v; }
+double to_f64(float2 v) { return (double)v.x + (double)v.y; }
+
+template <typename T>
+cudaError_t fetch_state(const T* d_U, const T* d_dU, size_t n, cudaStream_t st, double* U,
+                        double* dU) {
+    std::vector<T> a(n), b(n);
+    cudaError_t e = cudaMemcpyAsync(a.data(), d_U, n * sizeof(T), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.data(), d_dU, n * sizeof(T), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    for (size_t i = 0; i < n; ++i) {
+        U[i] = to_f64(a[i]);
+        dU[i] = to_f64(b[i]);
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int sfm_checkpoint(sfm_handle* h, void* buf, size_t* bytes) {
+    if (!h || !bytes) return fail(h, SFM_ERR_ARG, "sfm_checkpoint: bad arguments");
+    sfm_ext* x = ext(h);
+    if (x->ck_prec < 0) return fail(h, SFM_ERR_STATE, "sfm_checkpoint: no stepping state");
+    const size_t n = (size_t)x->ck_nshots * h->nstate;
+    const size_t need = 8 * sizeof(long long) + 2 * n * sizeof(double);
+    const size_t cap = *bytes;
+    *bytes = need;
+    if (!buf) return SFM_OK;
+    if (cap < need) return fail(h, SFM_ERR_ARG, "sfm_checkpoint: buffer too small");
+    CK(h, cudaSetDevice(h->device));
+    long long* hd = static_cast<long long*>(buf);
+    hd[0] = kCkMagic; hd[1] = kCkVersion; hd[2] = x->ck_nshots; hd[3] = h->nstate;
+    hd[4] = h->nsub; hd[5] = topology_fingerprint(h); hd[6] = x->ck_steps; hd[7] = x->ck_prec;
+    double* U = reinterpret_cast<double*>(hd + 8);
+    double* dU = U + n;
+    const int slot = x->ck_steps % 4;                   // U^n lives in buffer n mod 4
+    cudaError_t e;
+    if (x->ck_prec == SFM_FP64)
+        e = fetch_state(x->r64.U[slot], x->r64.dU, n, h->stream, U, dU);
+    else if (x->ck_prec == SFM_FP32X2)
+        e = fetch_state(x->r2.U[slot], x->r2.dU, n, h->stream, U, dU);
+    else
+        e = fetch_state(x->r32.U[slot], x->r32.dU, n, h->stream, U, dU);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sfm_checkpoint");
+    return SFM_OK;
+}
+
+extern "C" int sfm_restore(sfm_handle* h, const void* buf, size_t bytes) {
+    if (!h || !buf || bytes < 8 * sizeof(long long))
+        return fail(h, SFM_ERR_ARG, "sfm_restore: bad arguments");
+    if (h->nsub == 0) return fail(h, SFM_ERR_STATE, "sfm_restore: no topology");
+    const long long* hd = static_cast<const long long*>(buf);
+    if (hd[0] != kCkMagic || hd[1] != kCkVersion)
+        return fail(h, SFM_ERR_ARG, "sfm_restore: not a checkpoint of this format");
+    const long long nshots = hd[2];
+    if (nshots < 1 || hd[3] != h->nstate || hd[4] != h->nsub || hd[5] != topology_fingerprint(h))
+        return fail(h, SFM_ERR_ARG, "sfm_restore: checkpoint of a different topology");
+    const size_t n = (size_t)nshots * h->nstate;
+    if (bytes != 8 * sizeof(long long) + 2 * n * sizeof(double))
+        return fail(h, SFM_ERR_ARG, "sfm_restore: size does not match the header");
+    CK(h, cudaSetDevice(h->device));
+    const double* U = reinterpret_cast<const double*>(hd + 8);
+    CK(h, upload(h->d_init_U64, U, n, h->stream));
+    CK(h, upload(h->d_init_V64, U + n, n, h->stream));
+    h->init_nshots = (int)nshots;
+    h->have_init = true;
+    h->init_delta = true;
+    return SFM_OK;
 }
 
 // Largest eigenvalue of MM^{-1} KK.  One FP64 step of the stepping kernel

@@ -174,6 +174,7 @@ struct sfm_handle {
     double* d_init_V64 = nullptr;
     int init_nshots = 0;
     bool have_init = false;
+    bool init_delta = false;           // d_init_V64 holds delta^0 itself (sfm_restore)
     int4* d_rtab = nullptr;            // receiver pair table (readout_table)
     bool have_src = false, have_rec = false;
 

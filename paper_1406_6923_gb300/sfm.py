@@ -37,7 +37,7 @@ EXPORTS = ["sfm_create", "sfm_destroy", "sfm_last_error", "sfm_set_stream", "sfm
            "sfm_run", "sfm_cfl_dt", "sfm_last_launches", "sfm_debug_set", "sfm_set_model",
            "sfm_build_roms", "sfm_project_sources", "sfm_project_receivers", "sfm_free_build", "sfm_run_static",
            "sfm_autotune", "sfm_set_initial", "sfm_plan_pieces", "sfm_usable_depths",
-           "sfm_cut_depth"]
+           "sfm_cut_depth", "sfm_checkpoint", "sfm_restore"]
 
 
 class sfm_build_report(C.Structure):
@@ -95,6 +95,8 @@ def load(path=LIB_PATH):
         "sfm_plan_pieces": (_i, [_i, _i, _ip, _i, _ip, _ip, _i, _ip]),
         "sfm_usable_depths": (_i, [_i, _ip, _i, _dp, C.c_double, _ip]),
         "sfm_cut_depth": (_i, [_p, C.c_double, _ip, _i, _ip]),
+        "sfm_checkpoint": (_i, [_p, _p, C.POINTER(C.c_size_t)]),
+        "sfm_restore": (_i, [_p, _p, C.c_size_t]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -201,6 +203,21 @@ def sfm_run(h, precision, dt, nsteps, wavelet, nshots, nrec, traces=None, device
     _check(h, load().sfm_run(h, int(precision), float(dt), int(nsteps),
                              _p(w.ctypes.data), _p(out.ctypes.data), 0, C.byref(ms)))
     return out, ms.value
+
+
+def sfm_checkpoint(h):
+    """The stepping state of the last sfm_run as a bytes blob."""
+    need = C.c_size_t(0)
+    _check(h, load().sfm_checkpoint(h, None, C.byref(need)))
+    buf = np.zeros(need.value // 8, dtype=np.int64)     # 8-byte aligned
+    cap = C.c_size_t(buf.nbytes)
+    _check(h, load().sfm_checkpoint(h, buf.ctypes.data_as(_p), C.byref(cap)))
+    return buf.tobytes()
+
+
+def sfm_restore(h, blob):
+    buf = np.frombuffer(blob, dtype=np.int64).copy()
+    _check(h, load().sfm_restore(h, buf.ctypes.data_as(_p), buf.nbytes))
 
 
 def sfm_cfl_dt(h, iters=300):

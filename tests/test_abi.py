@@ -36,13 +36,20 @@ def test_last_error_without_handle_is_callable(lib):
     assert isinstance(lib.sfm_last_error(None), bytes)
 
 
-def test_binding_fails_loudly_without_the_library(tmp_path):
-    import importlib
+def test_binding_fails_loudly_without_the_library():
     from paper_1406_6923_gb300 import sfm
     saved = sfm._lib
     try:
         sfm._lib = None
         with pytest.raises(ImportError):
-            sfm.load(str(tmp_path / "missing.so"))
+            sfm.load(os.path.join(ROOT, "no_such_directory", "libsfm.so"))
     finally:
         sfm._lib = saved
+
+
+def test_checkpoint_calls_reject_a_null_handle(lib):
+    import ctypes as C
+    from paper_1406_6923_gb300 import sfm
+    n = C.c_size_t(0)
+    assert lib.sfm_checkpoint(None, None, C.byref(n)) == sfm.SFM_ERR_ARG
+    assert lib.sfm_restore(None, None, 0) == sfm.SFM_ERR_ARG
