@@ -2,6 +2,7 @@
 independent counts: the oracle's face topology and a direct count of the
 (receiver, subdomain) pairs."""
 import numpy as np
+import pytest
 
 import sfm_inputs as inputs
 from oracle import faces
@@ -46,3 +47,27 @@ def test_config2_bytes_per_step():
     assert bench.algorithmic_bytes_per_step(p, 1, rec, 8) == 2 * want
     # more shots add only the per-shot state
     assert (bench.algorithmic_bytes_per_step(p, 3, rec, 4) - want) == 2 * 512 * (4 * 16 * 48 + 2 * 48) * 4
+
+
+@pytest.mark.slow
+def test_reference_arm_prints_one_contract_line():
+    """``bench.py --impl reference`` (the FP64 oracle on a bounded sample of
+    the config-2 stepping) prints one JSON line with the contract's keys."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "0", "--cpu-sample-steps", "20"],
+                       capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"].startswith("cfg2")
