@@ -1,6 +1,7 @@
-"""The byte counts behind bench.py's roofline, checked on the CPU against
-independent counts: the oracle's face topology and a direct count of the
-(receiver, subdomain) pairs."""
+"""bench.py on the CPU: the byte counts behind its roofline, checked
+against independent counts (the oracle's face topology and a direct count
+of the (receiver, subdomain) pairs), and the JSON line of its reference
+arm."""
 import numpy as np
 import pytest
 
