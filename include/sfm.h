@@ -191,7 +191,9 @@ int sfm_cfl_dt(sfm_handle* h, int iters, double* lambda_max, double* dt_cfl);
  * candidate block shape - consumer warps in {2,4,6,8} times
  * coefficient ring stages in {2,3,4,6,8,12,16}, those whose shared memory
  * fits (for SFM_FP32F only stage counts that are multiples of the warps) -
- * steps the coupled system `nsteps` steps from a zero source twice; the
+ * steps the coupled system `nsteps` steps from rest with a zero source
+ * twice (a state from sfm_set_initial or sfm_restore is left aside for
+ * the probes and kept for the next sfm_run); the
  * fastest (step kernel alone, CUDA events) becomes the shape of later
  * sfm_run calls in that precision.  Results do not depend on the shape:
  * every shape sums in the same order.  Outputs: the chosen consumer warps,

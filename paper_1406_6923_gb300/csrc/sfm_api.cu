@@ -888,13 +888,22 @@ extern "C" int sfm_autotune(sfm_handle* h, int precision, int nsteps, int* ncw, 
     if (nsteps < 1) return fail(h, SFM_ERR_ARG, "sfm_autotune: nsteps < 1");
     CK(h, cudaSetDevice(h->device));
     ext(h)->ck_prec = -1;                  // the probes overwrite the run buffers
-    if (precision == SFM_FP64) return autotune_impl<sfm::PolF64>(h, nsteps, ncw, nstage, us_per_step);
-    if (precision == SFM_FP32) return autotune_impl<sfm::PolF32>(h, nsteps, ncw, nstage, us_per_step);
-    if (precision == SFM_FP32X2)
-        return autotune_impl<sfm::PolF32x2>(h, nsteps, ncw, nstage, us_per_step);
-    if (precision == SFM_FP32F)
-        return autotune_impl<sfm::PolF32F>(h, nsteps, ncw, nstage, us_per_step);
-    return fail(h, SFM_ERR_ARG, "sfm_autotune: unknown precision");
+    // the probes step from rest (dt = 1 is far above the stability limit
+    // for any nonzero state); an initial or restored state is kept for the
+    // next sfm_run
+    const bool had_init = h->have_init;
+    h->have_init = false;
+    int rc;
+    if (precision == SFM_FP64) rc = autotune_impl<sfm::PolF64>(h, nsteps, ncw, nstage, us_per_step);
+    else if (precision == SFM_FP32) rc = autotune_impl<sfm::PolF32>(h, nsteps, ncw, nstage, us_per_step);
+    else if (precision == SFM_FP32X2)
+        rc = autotune_impl<sfm::PolF32x2>(h, nsteps, ncw, nstage, us_per_step);
+    else if (precision == SFM_FP32F)
+        rc = autotune_impl<sfm::PolF32F>(h, nsteps, ncw, nstage, us_per_step);
+    else
+        rc = fail(h, SFM_ERR_ARG, "sfm_autotune: unknown precision");
+    h->have_init = had_init;
+    return rc;
 }
 
 // ---------------------------------------------------------------------------
