@@ -1,0 +1,51 @@
+"""The stand-in of the paper's own experiment (7 x 7 x 3 unit cubes, c(x, y)
+with a slow fracture, dimensionless units) through the GPU builder and the
+stepping, at the block width the GPU path takes (m = 10, b = 60) on a
+coarser copy of the layout (10^3-cell cubes), against the oracle.
+
+Marked ``gpu_pending``: written before any GPU run of this layout (its
+small shift makes the CG solves of the builder the slowest yet), so it is
+not among the ``-m gpu`` tests yet; run it with ``-m gpu_pending`` on a
+GPU."""
+import numpy as np
+import pytest
+
+import sfm_inputs as inputs
+from oracle import coupled, pipeline
+
+pytestmark = pytest.mark.gpu_pending
+
+
+@pytest.fixture(scope="module")
+def sfm():
+    import os
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1406_6923_gb300 import _build, sfm as mod
+    if not os.path.exists(mod.LIB_PATH):
+        _build.build()
+    mod.load()
+    return mod
+
+
+def test_paper_layout_builds_and_steps_like_the_oracle(sfm):
+    p = inputs.paper_layout(cells_per_unit=10, m=10, k=4)
+    rs = pipeline.build(p)
+    dt = pipeline.rom_dt(rs)
+    n = int(np.ceil(p.meta["t_end"] / dt))
+    w = inputs.wavelet_samples(p, dt, n)
+    ref = coupled.step_structured(rs, dt, n, w)
+    h = sfm.sfm_create(0)
+    try:
+        sfm.sfm_set_model(h, p.c, p.h, p.xcuts, p.ycuts, p.zcuts)
+        rep = sfm.sfm_build_roms(h, p.m_sub, p.k_sub, p.sigma, 1e-14)
+        sfm.sfm_project_sources(h, p.src_xyz, p.src_width)
+        sfm.sfm_project_receivers(h, p.rec_xyz)
+        got, _ = sfm.sfm_run(h, sfm.SFM_FP64, dt, n, w, rs.nshots, rs.nrec)
+        got_f, _ = sfm.sfm_run(h, sfm.SFM_FP32F, dt, n, w, rs.nshots, rs.nrec)
+    finally:
+        sfm.sfm_destroy(h)
+    assert rep["nregularized"] == 0
+    assert pipeline.rel_l2(got, ref) < 1e-8
+    assert pipeline.rel_l2(got_f, ref) < 1e-3
