@@ -353,19 +353,25 @@ int sfm_cut_depth(sfm_handle* h, double tau, int* depth_out, int depth_cap, int*
  * Work is enqueued on `stream` (a cudaStream_t, NULL for the legacy default
  * stream) and the call returns when it is done.
  *
- * Scratch memory: one static device array of 64 MiB per GPU, held by every
- * GPU that loads the library until the process exits; a problem whose
- * layout tables, tile-packed coefficients, state and partial receiver sums
- * need more returns SFM_ERR_ARG (sfm_last_error(NULL) gives the size
- * needed) before touching the device.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Every call
- * shares the one array and re-initialises what must start at zero, so calls
- * that overlap on the GPU (two streams, two host threads) race and must be
- * serialised by the caller.  No cudaMalloc, cudaFree or allocating library
- * routine is called.
- * Errors: SFM_ERR_ARG, SFM_ERR_CUDA, SFM_ERR_TIMEOUT, SFM_ERR_NOT_SPD,
- * SFM_ERR_UNSTABLE, reported through sfm_last_error(NULL).
+ * Scratch memory: one static device array of 64 MiB per GPU, held until
+ * the process exits.  It is reserved when the library's device code is
+ * loaded on that GPU; with lazy module loading (the CUDA runtime's default)
+ * that is the first call on the device, so make one warm-up call before
+ * another allocator takes the GPU's memory (a first call that finds no room
+ * returns SFM_ERR_CUDA), and before any stream capture.  Every call looks
+ * up the array's device address (cudaGetSymbolAddress) with `device`
+ * current.  A problem whose layout tables, tile-packed coefficients, state
+ * and partial receiver sums need more than 64 MiB returns SFM_ERR_ARG
+ * (sfm_last_error(NULL) gives the size needed) before touching the device.
+ * Every call shares the one array and re-initialises what must start at
+ * zero, so calls that overlap on the GPU (two streams, two host threads)
+ * race and must be serialised by the caller.  No cudaMalloc, cudaFree or
+ * allocating library routine is called.  The caller's current device is
+ * the same on return.
+ * Errors: SFM_ERR_ARG, SFM_ERR_CUDA (also an out-of-memory error on the
+ * first call on a device), SFM_ERR_TIMEOUT, SFM_ERR_NOT_SPD (checked before
+ * any stepping work), SFM_ERR_UNSTABLE, reported through
+ * sfm_last_error(NULL).
  */
 int sfm_run_static(int device, void* stream, int nsub, const int* k_sub, const int* m_face,
                    const int* nbr, const double* coeffs, int nshots, int nsrc_pairs,

@@ -7,19 +7,14 @@
 #include "sfm_internal.h"
 
 #include <algorithm>
-#include <mutex>
 #include <string>
 #include <vector>
 
 #define SFM_STATIC_SCRATCH_BYTES (64ull << 20)   // 64 MiB
-#define SFM_STATIC_MAX_DEVICES 64
 
 namespace {
 
 __device__ __align__(256) unsigned char g_static_scratch[SFM_STATIC_SCRATCH_BYTES];
-
-std::mutex g_static_mu;
-void* g_static_ptr[SFM_STATIC_MAX_DEVICES] = {nullptr};
 
 // failures are reported through sfm_last_error(NULL)
 int sfail(int code, const std::string& msg) {
@@ -27,21 +22,34 @@ int sfail(int code, const std::string& msg) {
     return code;
 }
 
-// Device address of the scratch array on the current device: looked up once
-// per device (with that device current) and cached.
-int scratch_address(int device, unsigned char** out) {
-    if (device < 0 || device >= SFM_STATIC_MAX_DEVICES) return sfail(SFM_ERR_ARG, "sfm_run_static: device index out of range");
-    std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_ptr[device]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess)
-            return sfail(SFM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        g_static_ptr[device] = p;
-    }
-    *out = static_cast<unsigned char*>(g_static_ptr[device]);
+// Device address of the scratch array in the current context, looked up on
+// every call (a table lookup once the module is loaded).  A cached address
+// would go stale if the caller reset the device and the module were loaded
+// again elsewhere.  With lazy module loading the first lookup on a device is
+// the one that loads the module and so reserves the array.
+int scratch_address(unsigned char** out) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess)
+        return sfail(SFM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    *out = static_cast<unsigned char*>(p);
     return SFM_OK;
 }
+
+// Makes `device` current for the scope and gives the caller's current device
+// back on every return path.
+struct DeviceScope {
+    int prev = -1;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceScope(int device) {
+        err = cudaGetDevice(&prev);
+        if (err != cudaSuccess) { prev = -1; return; }
+        if (prev != device) err = cudaSetDevice(device);
+    }
+    ~DeviceScope() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
 
 // Bump allocator over the scratch array (256-byte aligned pieces).
 struct Carve {
@@ -128,7 +136,11 @@ extern "C" int sfm_run_static(int device, void* stream, int nsub, const int* k_s
         std::vector<int> fill(cnt.begin(), cnt.end() - 1);
         for (int i = 0; i < nrec_pairs; ++i) pairs[fill[rec_id[i]]++] = i;
     }
-    // ---- block shape, grid and per-block pieces (host) ----
+    // ---- block shape, grid and per-block pieces, sized on `device` ----
+    if (device < 0) return sfail(SFM_ERR_ARG, "sfm_run_static: bad device");
+    DeviceScope dev(device);
+    if (dev.err != cudaSuccess)
+        return sfail(SFM_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(dev.err));
     const int ncw = 8, nstage = 6;
     int gmax = 0;
     if (sfm::step_max_grid<P>(ncw, sfm::step_smem_bytes<P>(kmax, bmax, nstage), &gmax) != 0)
@@ -169,10 +181,8 @@ extern "C" int sfm_run_static(int device, void* stream, int nsub, const int* k_s
                                       " bytes of scratch, the static limit is " +
                                       std::to_string(SFM_STATIC_SCRATCH_BYTES) + " bytes");
     // ---- device work: no allocation from here on ----
-    cudaError_t e = cudaSetDevice(device);
-    if (e != cudaSuccess) return sfail(SFM_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
     unsigned char* base = nullptr;
-    int rc = scratch_address(device, &base);
+    int rc = scratch_address(&base);
     if (rc != SFM_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
 #define SCK(call)                                                                              \
@@ -215,6 +225,16 @@ extern "C" int sfm_run_static(int device, void* stream, int nsub, const int* k_s
     SCK(sfm::launch_face_H(coeffs, (const long long*)at(o_g1), (const int*)at(o_b), (const int*)at(o_fo),
                            (const int*)at(o_nb), (const long long*)at(o_ho), (double*)at(o_H), nsub,
                            (int*)at(o_err), st));
+    {
+        // a face block that failed its Cholesky leaves its H_f unset: stop
+        // before any stepping work is enqueued
+        int herr0 = 0;
+        SCK(cudaMemcpyAsync(&herr0, at(o_err), sizeof(int), cudaMemcpyDeviceToHost, st));
+        SCK(cudaStreamSynchronize(st));
+        if (herr0 == SFM_ERR_NOT_SPD)
+            return sfail(SFM_ERR_NOT_SPD, "sfm_run_static: a face block of Gammahat_1 is not SPD");
+        if (herr0 != 0) return sfail(herr0, "sfm_run_static: device error in the face coupling");
+    }
     SCK(sfm::launch_pack_tiles<P>(coeffs, (const long long*)at(o_co), (const long long*)at(o_to),
                                   (const int*)at(o_b), (const int*)at(o_k), nsub, (double*)at(o_tiles), st));
     sfm::StepParams<double> p{};

@@ -3,9 +3,7 @@ sfm_restore) through the C ABI: an N-step run, its checkpoint and an M-step
 run from the restored state give the traces of one N+M-step run, which
 matches the oracle's stepping.
 
-Marked ``gpu_pending``: written before any GPU run of the calls, so it is
-not among the ``-m gpu`` tests yet; run it with ``-m gpu_pending`` on a
-GPU."""
+"""
 import numpy as np
 import pytest
 
@@ -14,7 +12,7 @@ from oracle import coupled, pipeline
 
 from rom_abi import load_into
 
-pytestmark = pytest.mark.gpu_pending
+pytestmark = pytest.mark.gpu
 
 N, M = 120, 180
 

@@ -1,19 +1,14 @@
 """The stand-in of the paper's own experiment (7 x 7 x 3 unit cubes, c(x, y)
 with a slow fracture, dimensionless units) through the GPU builder and the
 stepping, at the block width the GPU path takes (m = 10, b = 60) on a
-coarser copy of the layout (10^3-cell cubes), against the oracle.
-
-Marked ``gpu_pending``: written before any GPU run of this layout (its
-small shift makes the CG solves of the builder the slowest yet), so it is
-not among the ``-m gpu`` tests yet; run it with ``-m gpu_pending`` on a
-GPU."""
+coarser copy of the layout (10^3-cell cubes), against the oracle."""
 import numpy as np
 import pytest
 
 import sfm_inputs as inputs
 from oracle import coupled, pipeline
 
-pytestmark = pytest.mark.gpu_pending
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
@@ -46,6 +41,10 @@ def test_paper_layout_builds_and_steps_like_the_oracle(sfm):
         got_f, _ = sfm.sfm_run(h, sfm.SFM_FP32F, dt, n, w, rs.nshots, rs.nrec)
     finally:
         sfm.sfm_destroy(h)
-    assert rep["nregularized"] == 0
+    # the small shift leaves the last level's Gamma_k semidefinite (the
+    # constant mode is a near-pole at lambda = 0); the oracle clips its
+    # eigenvalues below zero and the builder projects a block that fails its
+    # Cholesky test the same way, at most one such block per subdomain here
+    assert rep["nregularized"] <= p.nsub
     assert pipeline.rel_l2(got, ref) < 1e-8
     assert pipeline.rel_l2(got_f, ref) < 1e-3

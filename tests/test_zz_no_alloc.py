@@ -1,14 +1,15 @@
 """sfm_run_static: the FP64 stepping without any device allocation, for
 callers that cannot allocate device memory when they step (their GPU memory
 is owned by another allocator, or cudaMalloc's implicit synchronisation is
-not acceptable in their loop).  Its traces must equal those of sfm_run, call
-after call, since both run the same kernels on the same inputs; its scratch
-lives in one static device array of fixed size."""
+not acceptable in their loop).  Its traces must equal those of sfm_run and of
+the FP64 oracle's coupled stepping, call after call; its scratch lives in one
+static device array of fixed size, so free device memory must not change
+across a call."""
 import numpy as np
 import pytest
 
 import sfm_inputs as inputs
-from oracle import pipeline
+from oracle import coupled, pipeline
 
 from rom_abi import abi_arrays, load_into
 
@@ -60,16 +61,25 @@ def test_static_entry_point_matches_sfm_run(sfm, problem):
     srows_d = torch.tensor(srows, dtype=torch.float64, device=dev)
     rrows_d = torch.tensor(rrows, dtype=torch.float64, device=dev)
     wav = torch.tensor(w, dtype=torch.float64, device=dev)
+    oracle_tr = coupled.step_structured(rs, dt, n, w)
     stream = torch.cuda.current_stream().cuda_stream
+    outs = [torch.full((nshots, nrec, n + 1), float("nan"), dtype=torch.float64, device=dev)
+            for _ in range(2)]
     for call in range(2):                      # two calls in a row share the scratch
-        out = torch.full((nshots, nrec, n + 1), float("nan"), dtype=torch.float64, device=dev)
+        out = outs[call]
         torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info(0)[0]
         sfm.sfm_run_static(0, stream, a["k_sub"], a["m_face"], a["nbr"], coeffs.data_ptr(), nshots,
                            sp_shot, sp_sub, srows_d.data_ptr(), nrec, rp_rec, rp_sub,
                            rrows_d.data_ptr(), dt, n, wav.data_ptr(), out.data_ptr())
+        torch.cuda.synchronize()
+        free_after = torch.cuda.mem_get_info(0)[0]
+        if call == 1:                          # the first call may load the module
+            assert free_after == free_before, (free_before, free_after)
         got = out.cpu().numpy()
         assert np.isfinite(got).all()
         assert np.linalg.norm(got - ref) <= FP64_TOL * np.linalg.norm(ref), call
+        assert np.linalg.norm(got - oracle_tr) <= FP64_TOL * np.linalg.norm(oracle_tr), call
 
 
 def test_static_entry_point_rejects_oversized_problems(sfm, problem):
