@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sfm", choices=["sfm", "reference"])
     ap.add_argument("--nsteps", type=int, default=None, help="time steps per run (default: 4000)")
-    ap.add_argument("--precision", default="auto", choices=["auto", "fp32f", "fp32", "fp32x2", "fp64"])
+    ap.add_argument("--precision", default="auto",
+                    choices=["auto", "fp32f", "tf32x3", "tf32", "fp32", "fp32x2", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=600)
     ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "paper"],
@@ -325,10 +326,10 @@ def main():
     run(sfm.SFM_FP64)
     torch.cuda.synchronize()
     ref = tr.cpu().numpy()
-    modes = {"fp32f": sfm.SFM_FP32F, "fp32": sfm.SFM_FP32, "fp32x2": sfm.SFM_FP32X2,
-             "fp64": sfm.SFM_FP64}
+    modes = {"fp32f": sfm.SFM_FP32F, "tf32x3": sfm.SFM_TF32X3, "tf32": sfm.SFM_TF32,
+             "fp32": sfm.SFM_FP32, "fp32x2": sfm.SFM_FP32X2, "fp64": sfm.SFM_FP64}
     errors = {"fp64": 0.0}
-    for name in ("fp32f", "fp32", "fp32x2"):
+    for name in ("fp32f", "tf32x3", "tf32", "fp32", "fp32x2"):
         try:
             run(modes[name])
             torch.cuda.synchronize()
@@ -336,7 +337,7 @@ def main():
         except sfm.SfmError as e:
             errors[name] = float("inf") if e.code == sfm.SFM_ERR_UNSTABLE else None
     if args.precision == "auto":
-        chosen = next(n for n in ("fp32f", "fp32", "fp32x2", "fp64")
+        chosen = next(n for n in ("fp32f", "tf32x3", "fp32", "fp32x2", "fp64")
                       if errors.get(n) is not None and errors[n] <= GATE)
     else:
         chosen = args.precision
@@ -393,7 +394,7 @@ def main():
 
     # roofline of the persistent stepping kernel
     pk, pk_kind = peaks()
-    word = {"fp32f": 4, "fp32": 4, "fp32x2": 8, "fp64": 8}[chosen]
+    word = {"fp32f": 4, "tf32x3": 4, "tf32": 4, "fp32": 4, "fp32x2": 8, "fp64": 8}[chosen]
     bytes_step = algorithmic_bytes_per_step(p, nshots, receiver_row_numbers(p), word)
     kms = statistics.mean(kern_ms)
     achieved = bytes_step * nsteps / (kms * 1e-3) / 1e9
@@ -414,7 +415,8 @@ def main():
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": {"fp32f": "f32", "fp32": "f32", "fp32x2": "f32x2", "fp64": "f64"}[chosen],
+           "vs_baseline": None, "dtype": {"fp32f": "f32", "tf32x3": "tf32x3", "tf32": "tf32", "fp32": "f32",
+                     "fp32x2": "f32x2", "fp64": "f64"}[chosen],
            "data": "synthetic",
            "config": {"workload": p.name, "cells": ncell, "subdomains": p.nsub,
                       "b": widths, "k": levels,

@@ -55,15 +55,39 @@ enum sfm_precision {
     SFM_FP32 = 1,            /* FP32 coefficients, state and sums              */
     SFM_FP32X2 = 2,          /* two-float numbers (hi + lo FP32, ~48-bit
                                 significand) with compensated FP32 arithmetic */
-    SFM_FP32F = 3            /* FP32 state and sums; each S-fraction block
+    SFM_FP32F = 3,           /* FP32 state and sums; each S-fraction block
                                 applied through its FP32 Cholesky factor,
                                 Gamma = L L^T (factored in FP64 on the GPU),
                                 which keeps it positive semi-definite under
                                 rounding                                       */
+    SFM_TF32X3 = 4,          /* multi-shot panels: shots stepped 16 at a time,
+                                every factor product L (L^T X) on the tensor
+                                cores with TF32 inputs split into head and
+                                tail words (3 products, FP32 accumulation);
+                                FP32 factors and state                         */
+    SFM_TF32 = 5,            /* as SFM_TF32X3 with single-word TF32 inputs
+                                (11 significant bits; deep ROMs diverge)       */
+    SFM_BF16 = 6             /* not built: sfm_run returns SFM_ERR_ARG (BF16's
+                                8-bit significand is coarser than TF32's)      */
 };
 
 /* flags for sfm_run */
 #define SFM_DEVICE_PTR 1     /* wavelet/traces are device pointers            */
+#define SFM_ENERGY 2         /* evaluate the discrete energy at the start and
+                                the end of the run (sfm_run_report)            */
+
+/* Report of the last sfm_run on a handle (sfm_run_report). */
+typedef struct sfm_run_info {
+    int precision;           /* precision of the run, -1 before the first one  */
+    int nsteps, nshots;
+    int launches;            /* device kernels launched by the call            */
+    double kernel_ms;        /* device time of the stepping kernel alone       */
+    double total_ms;         /* the whole call, host wall clock                */
+    int status;              /* the call's return code                         */
+    int unstable_step;       /* time step at which the instability sentinel
+                                stopped the run, -1 if it did not              */
+    int energy;              /* 1 if energies were evaluated (SFM_ENERGY)       */
+} sfm_run_info;
 
 /* Create a handle bound to CUDA device `device`.  *h receives the handle.
  * Errors: SFM_ERR_ARG (h NULL, bad device), SFM_ERR_CUDA. */
@@ -175,6 +199,24 @@ int sfm_set_initial(sfm_handle* h, int nshots, int npairs, const int* pair_shot,
  */
 int sfm_run(sfm_handle* h, int precision, double dt, int nsteps, const double* wavelet,
             double* traces, int flags, double* kernel_ms);
+
+/*
+ * Report of the last sfm_run (Stage 2's leapfrog and its conserved energy).
+ * info receives the run's precision, size, launches, timings, status and the
+ * sentinel's step: every step checks each updated face-block entry, and a
+ * non-finite value or one beyond 1e30 sets SFM_ERR_UNSTABLE and stops the
+ * persistent kernel at its next device-wide barrier, so a run above the CFL
+ * limit ends within a few steps of its blow-up instead of after nsteps.
+ * With SFM_ENERGY the run evaluated, in FP64 on the device, the discrete
+ * energy of the assembled leapfrog (Eqs. 17-19 as one system MM U'' = -KK U)
+ *     E^{n+1/2} = 1/2 (delta/dt)^T MM (delta/dt) + 1/2 (U^{n+1})^T KK U^n,
+ * delta = U^{n+1} - U^n, once for the starting state (n = -1: U^0 and
+ * delta^0) and once for the final one (n = N - 1); without a source term it
+ * is conserved.  energy[0 .. nshots-1] receives the start values and
+ * energy[nshots .. 2 nshots-1] the end values (capacity >= 2 nshots; NULL
+ * skips them).  Errors: SFM_ERR_ARG.
+ */
+int sfm_run_report(const sfm_handle* h, sfm_run_info* info, double* energy, int capacity);
 
 /*
  * Largest eigenvalue of the coupled ROM system's MM^{-1} KK and the leapfrog

@@ -70,6 +70,8 @@ struct PolF64 {
     __device__ static C zero() { return 0.0; }
     __device__ static C from_d(double x) { return x; }
     __host__ __device__ static double to_d(S x) { return x; }
+    // instability sentinel: false for a non-finite or runaway value
+    __device__ static bool sane(C v) { return fabs(v) < 1e30; }
     __device__ static C shfl_xor(C v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
     struct Acc {
         double s;
@@ -100,6 +102,7 @@ struct PolF32 {
     __device__ static C zero() { return 0.f; }
     __device__ static C from_d(double x) { return (float)x; }
     __host__ __device__ static double to_d(S x) { return x; }
+    __device__ static bool sane(C v) { return fabsf(v) < 1e30f; }
     __device__ static C shfl_xor(C v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
     struct Acc {
         float s;
@@ -143,6 +146,7 @@ struct PolF32x2 {
         return {h, (float)(x - (double)h)};
     }
     __host__ __device__ static double to_d(S x) { return (double)x.x + (double)x.y; }
+    __device__ static bool sane(C v) { return fabsf(v.hi) < 1e30f; }
     __device__ static C shfl_xor(C v, int o) {
         return {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
     }

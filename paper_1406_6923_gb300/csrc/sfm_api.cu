@@ -3,9 +3,13 @@
 #include "sfm_internal.h"
 
 #include <algorithm>
+#include <chrono>
+#include <climits>
+#include <type_traits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <string>
 #include <new>
 
 namespace {
@@ -82,7 +86,46 @@ namespace sfm {
 void set_global_error(const std::string& msg) { g_err = msg; }
 }  // namespace sfm
 
+// Data of the multi-shot panel modes (panel.cu), all FP32: padded factor
+// tiles, face blocks, source panels per (group, subdomain) unit, receiver
+// rows, and the per-subdomain receiver pair lists.
+struct PanelCache {
+    float *coef = nullptr, *H = nullptr, *src = nullptr, *rrows = nullptr;
+    long long *d_coef_off = nullptr, *d_src_off = nullptr;
+    int *d_sub_rp_ptr = nullptr, *d_sub_rp = nullptr;
+    int ngroups = 0, rpmax = 0;
+    bool valid = false;
+    void release() {
+        dfree(coef); dfree(H); dfree(src); dfree(rrows);
+        dfree(d_coef_off); dfree(d_src_off); dfree(d_sub_rp_ptr); dfree(d_sub_rp);
+        ngroups = rpmax = 0;
+        valid = false;
+    }
+};
+
+struct PanelBufs {
+    float *U = nullptr, *dU = nullptr, *mail[2] = {nullptr, nullptr}, *wav = nullptr,
+          *partial = nullptr;
+    size_t n_state = 0, n_mail = 0, n_wav = 0, n_part = 0;
+    void release() {
+        dfree(U); dfree(dU); dfree(mail[0]); dfree(mail[1]); dfree(wav); dfree(partial);
+        n_state = n_mail = n_wav = n_part = 0;
+    }
+};
+
 struct sfm_ext {
+    // report of the last sfm_run (sfm_run_report)
+    sfm_run_info info{-1, 0, 0, 0, 0.0, 0.0, 0, -1, 0};
+    std::vector<double> energy;        // E^{-1/2} then E^{N-1/2}, per shot
+    int* d_ustep = nullptr;            // instability sentinel step (INT_MAX: none)
+    PanelCache pc;
+    PanelBufs pb;
+    // panel block shape per mode (index 0: 1xTF32, 1: 3xTF32): consumer warps
+    // (16-shot groups per task) and ring stages; sfm_autotune overwrites them
+    int pncw[2] = {4, 4}, pnstage[2] = {4, 4};
+    int* d_task_ptr = nullptr;
+    int4* d_task = nullptr;
+    int task_grid = -1, task_ncw = -1, task_ngroups = -1;
     Cache<float> c32;
     Cache<double> c64;
     Cache<float2> c2;
@@ -110,6 +153,8 @@ struct sfm_ext {
 static sfm_ext* ext(sfm_handle* h) { return reinterpret_cast<sfm_ext*>(h->scratch); }
 
 static void invalidate(sfm_handle* h) {
+    ext(h)->pc.release();
+    ext(h)->task_grid = -1;
     ext(h)->c32.release();
     ext(h)->c64.release();
     ext(h)->c2.release();
@@ -155,6 +200,9 @@ int sfm_destroy(sfm_handle* h) {
     if (x) {
         x->c32.release(); x->c64.release(); x->c2.release(); x->c32f.release();
         x->r32.release(); x->r64.release(); x->r2.release();
+        x->pc.release(); x->pb.release();
+        dfree(x->d_ustep);
+        dfree(x->d_task_ptr); dfree(x->d_task);
         dfree(x->d_traces); dfree(x->d_bad); dfree(x->d_piece_ptr); dfree(x->d_prec);
         if (x->ev0) cudaEventDestroy(x->ev0);
         if (x->ev1) cudaEventDestroy(x->ev1);
@@ -462,11 +510,13 @@ int sfm_debug_set(sfm_handle* h, int key, long long value) {
     if (key == 3) {
         if (value < 1 || value > 8) return fail(h, SFM_ERR_ARG, "sfm_debug_set: consumer warps 1..8");
         for (int i = 0; i < 4; ++i) ext(h)->ncw[i] = (int)value;
+        for (int i = 0; i < 2; ++i) ext(h)->pncw[i] = (int)value;
         return SFM_OK;
     }
     if (key == 4) {
         if (value < 2 || value > 16) return fail(h, SFM_ERR_ARG, "sfm_debug_set: ring stages 2..16");
         for (int i = 0; i < 4; ++i) ext(h)->nstage[i] = (int)value;
+        for (int i = 0; i < 2; ++i) ext(h)->pnstage[i] = (int)value;
         return SFM_OK;
     }
     return fail(h, SFM_ERR_ARG, "sfm_debug_set: unknown key");
@@ -674,6 +724,75 @@ static int accel_f64(sfm_handle* h, const double* X, double* A, int* launches) {
     return SFM_OK;
 }
 
+// Discrete energy E = 1/2 (delta/dt)^T MM (delta/dt) + 1/2 U^T KK (U - delta)
+// per shot of a state (U, delta) in the state layout (energy.cu), in FP64;
+// the per-(subdomain, level) terms are added on the host in a fixed order.
+static int energy_f64(sfm_handle* h, const double* U, const double* D, int nshots, double dt,
+                      double* out) {
+    cudaStream_t st = h->stream;
+    const size_t nt = (size_t)nshots * h->nsub * h->kmax * 2;
+    double* d_t = nullptr;
+    CK(h, dalloc(d_t, nt));
+    std::vector<double> t(nt);
+    cudaError_t e = sfm::launch_energy_terms(h->d_coef64, h->d_coef_off, h->d_b, h->d_k, h->nsub,
+                                             h->kmax, nshots, U, D, h->nstate, h->d_state_off, d_t, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t.data(), d_t, nt * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dfree(d_t);
+    if (e != cudaSuccess) return cuda_fail(h, e, "energy");
+    for (int q = 0; q < nshots; ++q) {
+        double kin = 0.0, pot = 0.0;
+        for (int s = 0; s < h->nsub; ++s)
+            for (int j = 0; j < h->k[s]; ++j) {
+                const size_t i = (((size_t)q * h->nsub + s) * h->kmax + j) * 2;
+                kin += t[i];
+                pot += t[i + 1];
+            }
+        out[q] = 0.5 * kin / (dt * dt) + 0.5 * pot;
+    }
+    return SFM_OK;
+}
+
+template <typename T>
+static int energy_of(sfm_handle* h, const T* U, const T* D, int nshots, double dt, double* out) {
+    if constexpr (std::is_same<T, double>::value) {
+        return energy_f64(h, U, D, nshots, dt, out);
+    } else {
+        const size_t n = (size_t)nshots * h->nstate;
+        double *U64 = nullptr, *D64 = nullptr;
+        cudaError_t e = dalloc(U64, n);
+        if (e == cudaSuccess) e = dalloc(D64, n);
+        if (e == cudaSuccess) e = sfm::launch_state_to_f64<T>(U, U64, n, h->stream);
+        if (e == cudaSuccess) e = sfm::launch_state_to_f64<T>(D, D64, n, h->stream);
+        int rc = e == cudaSuccess ? energy_f64(h, U64, D64, nshots, dt, out) : cuda_fail(h, e, "energy");
+        dfree(U64);
+        dfree(D64);
+        return rc;
+    }
+}
+
+static int energy_of_panel(sfm_handle* h, const float* U, const float* D, int nshots, double dt,
+                           double* out) {
+    const size_t n = (size_t)nshots * h->nstate;
+    double *U64 = nullptr, *D64 = nullptr;
+    cudaError_t e = dalloc(U64, n);
+    if (e == cudaSuccess) e = dalloc(D64, n);
+    if (e == cudaSuccess) e = sfm::launch_from_panel(U, U64, nshots, h->nstate, h->stream);
+    if (e == cudaSuccess) e = sfm::launch_from_panel(D, D64, nshots, h->nstate, h->stream);
+    int rc = e == cudaSuccess ? energy_f64(h, U64, D64, nshots, dt, out) : cuda_fail(h, e, "energy");
+    dfree(U64);
+    dfree(D64);
+    return rc;
+}
+
+static int ensure_ustep(sfm_handle* h) {
+    sfm_ext* x = ext(h);
+    if (!x->d_ustep) CK(h, dalloc(x->d_ustep, 1));
+    const int big = INT_MAX;
+    CK(h, cudaMemcpyAsync(x->d_ustep, &big, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    return SFM_OK;
+}
+
 template <class P>
 static int run_impl(sfm_handle* h, double dt, int nsteps, const double* wavelet, double* traces,
                     int flags, double* kernel_ms) {
@@ -757,6 +876,13 @@ static int run_impl(sfm_handle* h, double dt, int nsteps, const double* wavelet,
     CK(h, cudaMemsetAsync(h->d_bar, 0, sizeof(unsigned int), st));
     CK(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
     CK(h, cudaMemsetAsync(x->d_bad, 0, sizeof(int), st));
+    if (flags & SFM_ENERGY) {
+        x->energy.assign(2 * (size_t)h->nshots, 0.0);
+        rc = energy_of<T>(h, r.U[0], r.dU, h->nshots, dt, x->energy.data());
+        if (rc != SFM_OK) { dfree(tmp64); return rc; }
+    }
+    rc = ensure_ustep(h);
+    if (rc != SFM_OK) { dfree(tmp64); return rc; }
 
     sfm::StepParams<T> p{};
     p.nsub = h->nsub; p.nshots = h->nshots; p.nunits = h->nshots * h->nsub; p.nsteps = nsteps;
@@ -775,6 +901,7 @@ static int run_impl(sfm_handle* h, double dt, int nsteps, const double* wavelet,
     p.bar = h->d_bar; p.err = h->d_err; p.timeout_ns = x->timeout_ns;
     p.skip_arrive = x->skip_arrive;
     p.Kx = nullptr;
+    p.ustep = x->d_ustep;
 
     int grid = 0;
     rc = step_setup<P>(h, p.nunits, h->src_off.data(), p, &grid);
@@ -794,18 +921,295 @@ static int run_impl(sfm_handle* h, double dt, int nsteps, const double* wavelet,
     CK(h, cudaMemcpyAsync(&bad, x->d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
     if (!(flags & SFM_DEVICE_PTR))
         CK(h, cudaMemcpyAsync(traces, d_traces, ntr * sizeof(double), cudaMemcpyDeviceToHost, st));
+    int ustep = INT_MAX;
+    CK(h, cudaMemcpyAsync(&ustep, x->d_ustep, sizeof(int), cudaMemcpyDeviceToHost, st));
     e = cudaStreamSynchronize(st);
     dfree(tmp64);
     if (e != cudaSuccess) return cuda_fail(h, e, "stepping");
     h->last_launches = launches;
+    x->info.unstable_step = ustep == INT_MAX ? -1 : ustep;
     if (kernel_ms) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, x->ev0, x->ev1);
         *kernel_ms = ms;
     }
     if (herr == SFM_ERR_TIMEOUT) return fail(h, SFM_ERR_TIMEOUT, "device-wide barrier timed out");
+    if (herr == SFM_ERR_UNSTABLE)
+        return fail(h, SFM_ERR_UNSTABLE, "unstable: the state ran away at step " +
+                                             std::to_string(x->info.unstable_step) +
+                                             " (time step above the CFL limit?)");
     if (herr != 0) return fail(h, herr, "device error during stepping");
     if (bad) return fail(h, SFM_ERR_UNSTABLE, "non-finite traces (time step above the CFL limit?)");
+    if (flags & SFM_ENERGY) {
+        rc = energy_of<T>(h, r.U[nsteps & 3], r.dU, h->nshots, dt, x->energy.data() + h->nshots);
+        if (rc != SFM_OK) return rc;
+    }
+    return SFM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Multi-shot panel modes (SFM_TF32X3, SFM_TF32): shots stepped 16 at a time
+// with tensor-core factor products (panel.cu).
+
+static int panel_mode_of(int precision) { return precision == SFM_TF32X3 ? 3 : 1; }
+static int panel_slot(int mode) { return mode == 3 ? 1 : 0; }
+
+// FP32 data of the panel path, built once per set of coefficients, sources
+// and receivers: the FP32 Cholesky factors (factored in FP64) in 72-float
+// padded tiles, H_f and the receiver rows in FP32, the source rows of every
+// (shot, subdomain) pair in the panel of its (group, subdomain) unit.
+static int prepare_panel(sfm_handle* h) {
+    sfm_ext* x = ext(h);
+    PanelCache& c = x->pc;
+    const int ngroups = (h->nshots + 15) / 16;
+    if (c.valid && c.ngroups == ngroups) return SFM_OK;
+    c.release();
+    cudaStream_t st = h->stream;
+    const long long ntiles = h->ntcoef / 64;
+    float* tmp = nullptr;
+    CK(h, dalloc(tmp, (size_t)h->ntcoef));
+    int bad = 0;
+    cudaError_t e = cudaMemsetAsync(x->d_bad, 0, sizeof(int), st);
+    if (e == cudaSuccess)
+        e = sfm::launch_factor_tiles(h->d_coef64, h->d_coef_off, h->d_tcoef_off, h->d_b, h->d_k,
+                                     h->nsub, h->kmax, tmp, x->d_bad, st);
+    if (e == cudaSuccess) e = dalloc(c.coef, (size_t)ntiles * 72);
+    if (e == cudaSuccess) e = sfm::launch_pad_tiles(tmp, c.coef, ntiles, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, x->d_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dfree(tmp);
+    if (e != cudaSuccess) { c.release(); return cuda_fail(h, e, "panel factors"); }
+    if (bad) {
+        c.release();
+        return fail(h, SFM_ERR_NOT_SPD, "panel modes: an S-fraction block is not positive definite");
+    }
+    std::vector<long long> coff(h->nsub);
+    for (int s = 0; s < h->nsub; ++s) coff[s] = h->tcoef_off[s] / 64 * 72;
+    CK(h, upload(c.d_coef_off, coff.data(), coff.size(), st));
+    CK(h, dalloc(c.H, (size_t)h->nH));
+    CK(h, sfm::launch_convert<sfm::PolF32F>(h->d_H64, c.H, (size_t)h->nH, st));
+    CK(h, dalloc(c.rrows, (size_t)h->nrrow));
+    CK(h, sfm::launch_convert<sfm::PolF32F>(h->d_rrows64, c.rrows, (size_t)h->nrrow, st));
+    // source panels
+    std::vector<long long> poff((size_t)ngroups * h->nsub, -1), off64, dst;
+    std::vector<int> len;
+    long long total = 0;
+    for (int q = 0; q < h->nshots; ++q)
+        for (int s = 0; s < h->nsub; ++s) {
+            const long long so = h->src_off[(size_t)q * h->nsub + s];
+            if (so < 0) continue;
+            long long& po = poff[(size_t)(q / 16) * h->nsub + s];
+            if (po < 0) { po = total; total += (long long)h->k[s] * h->b[s] * 16; }
+            const int c16 = q % 16;
+            off64.push_back(so);
+            dst.push_back(po + 2 * (c16 & 7) + (c16 >> 3));
+            len.push_back(h->k[s] * h->b[s]);
+        }
+    CK(h, upload(c.d_src_off, poff.data(), poff.size(), st));
+    CK(h, dalloc(c.src, (size_t)std::max<long long>(total, 1)));
+    if (total) CK(h, cudaMemsetAsync(c.src, 0, (size_t)total * sizeof(float), st));
+    if (!off64.empty()) {
+        long long *d_o = nullptr, *d_d = nullptr;
+        int* d_l = nullptr;
+        e = upload(d_o, off64.data(), off64.size(), st);
+        if (e == cudaSuccess) e = upload(d_d, dst.data(), dst.size(), st);
+        if (e == cudaSuccess) e = upload(d_l, len.data(), len.size(), st);
+        if (e == cudaSuccess) e = sfm::launch_src_panels(h->d_src64, d_o, d_d, d_l, (int)off64.size(), c.src, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        dfree(d_o); dfree(d_d); dfree(d_l);
+        if (e != cudaSuccess) { c.release(); return cuda_fail(h, e, "panel sources"); }
+    }
+    // receiver pairs by subdomain
+    std::vector<int> ptr(h->nsub + 1, 0), list(std::max(h->nrpairs, 1));
+    for (int i = 0; i < h->nrpairs; ++i) ptr[h->rp_sub[i] + 1]++;
+    for (int s = 0; s < h->nsub; ++s) ptr[s + 1] += ptr[s];
+    {
+        std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+        for (int i = 0; i < h->nrpairs; ++i) list[fill[h->rp_sub[i]]++] = i;
+    }
+    int rpmax = 0;
+    for (int s = 0; s < h->nsub; ++s) rpmax = std::max(rpmax, ptr[s + 1] - ptr[s]);
+    CK(h, upload(c.d_sub_rp_ptr, ptr.data(), ptr.size(), st));
+    CK(h, upload(c.d_sub_rp, list.data(), list.size(), st));
+    c.ngroups = ngroups;
+    c.rpmax = rpmax;
+    c.valid = true;
+    return SFM_OK;
+}
+
+// Block shape, grid and task table of the panel kernel for this handle.
+static int panel_setup(sfm_handle* h, int mode, int* grid_out, int* ncw_out, int* nstage_out) {
+    sfm_ext* x = ext(h);
+    const int slot = panel_slot(mode);
+    const int ngroups = x->pc.ngroups;
+    const int ncw = std::max(1, std::min(x->pncw[slot], std::min(ngroups, sfm::PANEL_NCW_MAX)));
+    const int nstage = x->pnstage[slot];
+    const size_t smem = sfm::panel_smem_bytes(ncw, nstage, h->bmax, x->pc.rpmax);
+    int gmax = 0;
+    if (sfm::panel_max_grid(mode, ncw, smem, &gmax) != 0)
+        return fail(h, SFM_ERR_ARG, "panel modes: blocks too large for shared memory");
+    const long long ntasks = (long long)h->nsub * ((ngroups + ncw - 1) / ncw);
+    const int grid = (int)std::max(1LL, std::min<long long>(gmax, ntasks));
+    if (grid != x->task_grid || ncw != x->task_ncw || ngroups != x->task_ngroups) {
+        std::vector<int> ptr;
+        std::vector<int4> tasks;
+        sfm::build_panel_tasks(h->nsub, ngroups, h->k.data(), h->b.data(), ncw, grid, ptr, tasks);
+        CK(h, upload(x->d_task_ptr, ptr.data(), ptr.size(), h->stream));
+        CK(h, upload(x->d_task, tasks.data(), tasks.size(), h->stream));
+        x->task_grid = grid;
+        x->task_ncw = ncw;
+        x->task_ngroups = ngroups;
+    }
+    *grid_out = grid;
+    *ncw_out = ncw;
+    *nstage_out = nstage;
+    return SFM_OK;
+}
+
+// The panel run: like run_impl, with the state, face data, wavelet and
+// readout sums in panel form.  zero_source: a probe with a zero wavelet
+// from rest (sfm_autotune), leaving any initial state aside.
+static int run_panel_impl(sfm_handle* h, int mode, double dt, int nsteps, const double* wavelet,
+                          double* traces, int flags, double* kernel_ms, bool zero_source = false) {
+    sfm_ext* x = ext(h);
+    int rc = prepare_panel(h);
+    if (rc != SFM_OK) return rc;
+    PanelCache& c = x->pc;
+    PanelBufs& r = x->pb;
+    cudaStream_t st = h->stream;
+    const int ngroups = c.ngroups;
+    const size_t nst = (size_t)ngroups * h->nstate * 16;
+    const size_t nml = (size_t)ngroups * h->nmail * 16;
+    const size_t nwav = (size_t)ngroups * 16 * nsteps;
+    const size_t npart = (size_t)ngroups * (nsteps + 1) * std::max(h->nrpairs, 1) * 16;
+    const size_t ntr = (size_t)h->nshots * h->nrec * (nsteps + 1);
+    { size_t hs = r.n_state; CK(h, grow(r.U, hs, nst)); }
+    { size_t hs = r.n_state; CK(h, grow(r.dU, hs, nst)); r.n_state = hs; }
+    { size_t hm = r.n_mail; CK(h, grow(r.mail[0], hm, nml)); }
+    { size_t hm = r.n_mail; CK(h, grow(r.mail[1], hm, nml)); r.n_mail = hm; }
+    CK(h, grow(r.wav, r.n_wav, nwav));
+    CK(h, grow(r.partial, r.n_part, npart));
+    double* d_traces = traces;
+    if (!(flags & SFM_DEVICE_PTR)) {
+        CK(h, grow(x->d_traces, x->n_traces, ntr));
+        d_traces = x->d_traces;
+    }
+    int launches = 0;
+    CK(h, cudaMemsetAsync(r.wav, 0, nwav * sizeof(float), st));
+    if (!zero_source) {
+        const size_t nw64 = (size_t)h->nshots * nsteps;
+        const double* d_wav64 = wavelet;
+        double* tmp64 = nullptr;
+        if (!(flags & SFM_DEVICE_PTR)) {
+            CK(h, dalloc(tmp64, nw64));
+            cudaError_t e = cudaMemcpyAsync(tmp64, wavelet, nw64 * sizeof(double), cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) { dfree(tmp64); return cuda_fail(h, e, "wavelet"); }
+            d_wav64 = tmp64;
+        }
+        cudaError_t e = sfm::launch_convert<sfm::PolF32F>(d_wav64, r.wav, nw64, st);
+        if (e == cudaSuccess && tmp64) e = cudaStreamSynchronize(st);
+        dfree(tmp64);
+        if (e != cudaSuccess) return cuda_fail(h, e, "wavelet");
+        ++launches;
+    }
+    CK(h, cudaMemsetAsync(r.U, 0, nst * sizeof(float), st));
+    CK(h, cudaMemsetAsync(r.dU, 0, nst * sizeof(float), st));
+    if (h->have_init && !zero_source) {
+        if (h->init_nshots != h->nshots)
+            return fail(h, SFM_ERR_STATE, "sfm_run: initial state set for a different shot count");
+        if (h->init_delta) {
+            // restored U^0 and delta^0
+            CK(h, sfm::launch_to_panel(h->d_init_U64, r.U, h->nshots, h->nstate, st));
+            CK(h, sfm::launch_to_panel(h->d_init_V64, r.dU, h->nshots, h->nstate, st));
+            launches += 2;
+        } else {
+            // delta^0 = dt V^0 - dt^2/2 a_hom(U^0), in FP64 (Algorithm 1 step 1.4)
+            const size_t n64 = (size_t)h->nshots * h->nstate;
+            double *A = nullptr, *D = nullptr;
+            cudaError_t e0 = dalloc(A, n64);
+            if (e0 == cudaSuccess) e0 = dalloc(D, n64);
+            if (e0 != cudaSuccess) { dfree(A); dfree(D); return cuda_fail(h, e0, "initial state"); }
+            rc = accel_f64(h, h->d_init_U64, A, &launches);
+            cudaError_t e1 = cudaSuccess;
+            if (rc == SFM_OK) {
+                if ((e1 = sfm::launch_start_delta(h->d_init_V64, A, dt, n64, D, st)) == cudaSuccess &&
+                    (e1 = sfm::launch_to_panel(h->d_init_U64, r.U, h->nshots, h->nstate, st)) == cudaSuccess &&
+                    (e1 = sfm::launch_to_panel(D, r.dU, h->nshots, h->nstate, st)) == cudaSuccess)
+                    e1 = cudaStreamSynchronize(st);
+                launches += 3;
+            }
+            dfree(A);
+            dfree(D);
+            if (rc != SFM_OK) return rc;
+            if (e1 != cudaSuccess) return cuda_fail(h, e1, "initial state");
+        }
+    }
+    if (flags & SFM_ENERGY) {
+        x->energy.assign(2 * (size_t)h->nshots, 0.0);
+        rc = energy_of_panel(h, r.U, r.dU, h->nshots, dt, x->energy.data());
+        if (rc != SFM_OK) return rc;
+    }
+    rc = ensure_ustep(h);
+    if (rc != SFM_OK) return rc;
+    int grid = 0, ncw = 0, nstage = 0;
+    rc = panel_setup(h, mode, &grid, &ncw, &nstage);
+    if (rc != SFM_OK) return rc;
+    CK(h, cudaMemsetAsync(h->d_bar, 0, sizeof(unsigned int), st));
+    CK(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+    CK(h, cudaMemsetAsync(x->d_bad, 0, sizeof(int), st));
+    sfm::PanelParams p{};
+    p.nsub = h->nsub; p.ngroups = ngroups; p.nsteps = nsteps;
+    p.ncw = ncw; p.nstage = nstage; p.bmax = h->bmax; p.rpmax = c.rpmax;
+    p.nstate = h->nstate; p.nmail = h->nmail;
+    p.task_ptr = x->d_task_ptr; p.task = x->d_task;
+    p.coef_off = c.d_coef_off; p.coef = c.coef;
+    p.state_off = h->d_state_off; p.mail_off = h->d_mail_off; p.frow = h->d_frow; p.H = c.H;
+    p.src_off = c.d_src_off; p.src = c.src; p.wavelet = r.wav;
+    p.sub_rp_ptr = c.d_sub_rp_ptr; p.sub_rp = c.d_sub_rp; p.rp_off = h->d_rp_off; p.rrows = c.rrows;
+    p.nrpairs = h->nrpairs; p.partial = r.partial;
+    p.U = r.U; p.dU = r.dU; p.mail0 = r.mail[0]; p.mail1 = r.mail[1];
+    p.dt2 = (float)(dt * dt);
+    p.bar = h->d_bar; p.err = h->d_err; p.timeout_ns = x->timeout_ns; p.skip_arrive = x->skip_arrive;
+    p.ustep = x->d_ustep;
+    CK(h, cudaEventRecord(x->ev0, st));
+    cudaError_t e = sfm::launch_panel(mode, p, grid, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "panel kernel launch");
+    ++launches;
+    CK(h, cudaEventRecord(x->ev1, st));
+    if (h->nrpairs > 0) {
+        CK(h, sfm::launch_panel_traces(r.partial, h->d_rec_ptr, h->d_rec_pairs, h->nshots, nsteps,
+                                       h->nrec, h->nrpairs, d_traces, x->d_bad, st));
+    } else {
+        CK(h, cudaMemsetAsync(d_traces, 0, ntr * sizeof(double), st));
+    }
+    ++launches;
+    int herr = 0, bad = 0;
+    CK(h, cudaMemcpyAsync(&herr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(h, cudaMemcpyAsync(&bad, x->d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (!(flags & SFM_DEVICE_PTR))
+        CK(h, cudaMemcpyAsync(traces, d_traces, ntr * sizeof(double), cudaMemcpyDeviceToHost, st));
+    int ustep = INT_MAX;
+    CK(h, cudaMemcpyAsync(&ustep, x->d_ustep, sizeof(int), cudaMemcpyDeviceToHost, st));
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "panel stepping");
+    h->last_launches = launches;
+    x->info.unstable_step = ustep == INT_MAX ? -1 : ustep;
+    if (kernel_ms) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, x->ev0, x->ev1);
+        *kernel_ms = ms;
+    }
+    if (herr == SFM_ERR_TIMEOUT) return fail(h, SFM_ERR_TIMEOUT, "device-wide barrier timed out");
+    if (herr == SFM_ERR_UNSTABLE)
+        return fail(h, SFM_ERR_UNSTABLE, "unstable: the state ran away at step " +
+                                             std::to_string(x->info.unstable_step) +
+                                             " (time step above the CFL limit?)");
+    if (herr != 0) return fail(h, herr, "device error during stepping");
+    if (bad) return fail(h, SFM_ERR_UNSTABLE, "non-finite traces (time step above the CFL limit?)");
+    if ((flags & SFM_ENERGY) && !zero_source) {
+        rc = energy_of_panel(h, r.U, r.dU, h->nshots, dt, x->energy.data() + h->nshots);
+        if (rc != SFM_OK) return rc;
+    }
     return SFM_OK;
 }
 
@@ -819,6 +1223,12 @@ extern "C" int sfm_run(sfm_handle* h, int precision, double dt, int nsteps, cons
     CK(h, cudaSetDevice(h->device));
     sfm_ext* x = ext(h);
     x->ck_prec = -1;
+    const auto t0 = std::chrono::steady_clock::now();
+    x->info = sfm_run_info{precision, nsteps, h->nshots, 0, 0.0, 0.0, 0, -1, 0};
+    if (!(flags & SFM_ENERGY)) x->energy.clear();
+    double kms = 0.0;
+    kernel_ms = kernel_ms ? kernel_ms : &kms;
+    *kernel_ms = 0.0;
     int rc;
     if (precision == SFM_FP64)
         rc = run_impl<sfm::PolF64>(h, dt, nsteps, wavelet, traces, flags, kernel_ms);
@@ -828,14 +1238,37 @@ extern "C" int sfm_run(sfm_handle* h, int precision, double dt, int nsteps, cons
         rc = run_impl<sfm::PolF32x2>(h, dt, nsteps, wavelet, traces, flags, kernel_ms);
     else if (precision == SFM_FP32F)
         rc = run_impl<sfm::PolF32F>(h, dt, nsteps, wavelet, traces, flags, kernel_ms);
+    else if (precision == SFM_TF32X3 || precision == SFM_TF32)
+        rc = run_panel_impl(h, panel_mode_of(precision), dt, nsteps, wavelet, traces, flags, kernel_ms);
+    else if (precision == SFM_BF16)
+        return fail(h, SFM_ERR_ARG, "sfm_run: BF16 products are not built (an 8-bit significand "
+                                    "is coarser than TF32's 11 bits, with which the factored "
+                                    "stepping of deep ROMs already diverges)");
     else
         return fail(h, SFM_ERR_ARG, "sfm_run: unknown precision");
+    x->info.status = rc;
+    x->info.launches = h->last_launches;
+    x->info.kernel_ms = *kernel_ms;
+    x->info.total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    x->info.energy = (rc == SFM_OK && (flags & SFM_ENERGY)) ? 1 : 0;
     if (rc == SFM_OK) {
         x->ck_prec = precision;
         x->ck_steps = nsteps;
         x->ck_nshots = h->nshots;
     }
     return rc;
+}
+
+extern "C" int sfm_run_report(const sfm_handle* h, sfm_run_info* info, double* energy, int capacity) {
+    if (!h || !info) return fail(nullptr, SFM_ERR_ARG, "sfm_run_report: bad arguments");
+    const sfm_ext* x = reinterpret_cast<const sfm_ext*>(h->scratch);
+    *info = x->info;
+    if (energy && x->info.energy) {
+        if (capacity < (int)x->energy.size())
+            return fail(nullptr, SFM_ERR_ARG, "sfm_run_report: energy capacity below 2 * nshots");
+        std::copy(x->energy.begin(), x->energy.end(), energy);
+    }
+    return SFM_OK;
 }
 
 // Shape search for the stepping kernel: every candidate (consumer warps,
@@ -880,6 +1313,46 @@ static int autotune_impl(sfm_handle* h, int nsteps, int* ncw_out, int* nstage_ou
     return SFM_OK;
 }
 
+// The same search for the panel modes: 16-shot groups per task (consumer
+// warps) in {1, 2, 4, 8} up to the number of groups, ring stages in
+// {2, 3, 4, 6, 8}, each timed on zero-source probes from rest.
+static int autotune_panel(sfm_handle* h, int mode, int nsteps, int* ncw_out, int* nstage_out,
+                          double* us_out) {
+    static const int kNcw[] = {1, 2, 4, 8};
+    static const int kStage[] = {2, 3, 4, 6, 8};
+    sfm_ext* x = ext(h);
+    int rc = prepare_panel(h);
+    if (rc != SFM_OK) return rc;
+    const int slot = panel_slot(mode);
+    const int ncw0 = x->pncw[slot], nst0 = x->pnstage[slot];
+    std::vector<double> tr((size_t)h->nshots * h->nrec * (nsteps + 1));
+    double best = 1e300;
+    int bn = ncw0, bs = nst0;
+    for (int nc : kNcw) {
+        if (nc > 1 && nc > x->pc.ngroups) continue;
+        for (int ns : kStage) {
+            int gmax = 0;
+            if (sfm::panel_max_grid(mode, nc, sfm::panel_smem_bytes(nc, ns, h->bmax, x->pc.rpmax), &gmax) != 0 ||
+                gmax < 1)
+                continue;
+            x->pncw[slot] = nc;
+            x->pnstage[slot] = ns;
+            double ms = 0.0, ms2 = 0.0;
+            rc = run_panel_impl(h, mode, 1.0, nsteps, nullptr, tr.data(), 0, &ms, true);
+            if (rc == SFM_OK) rc = run_panel_impl(h, mode, 1.0, nsteps, nullptr, tr.data(), 0, &ms2, true);
+            if (rc != SFM_OK) { x->pncw[slot] = ncw0; x->pnstage[slot] = nst0; return rc; }
+            ms = std::min(ms, ms2);
+            if (ms < best) { best = ms; bn = nc; bs = ns; }
+        }
+    }
+    x->pncw[slot] = bn;
+    x->pnstage[slot] = bs;
+    if (ncw_out) *ncw_out = bn;
+    if (nstage_out) *nstage_out = bs;
+    if (us_out) *us_out = best * 1e3 / nsteps;
+    return SFM_OK;
+}
+
 extern "C" int sfm_autotune(sfm_handle* h, int precision, int nsteps, int* ncw, int* nstage,
                             double* us_per_step) {
     if (!h) return fail(nullptr, SFM_ERR_ARG, "NULL handle");
@@ -900,6 +1373,8 @@ extern "C" int sfm_autotune(sfm_handle* h, int precision, int nsteps, int* ncw, 
         rc = autotune_impl<sfm::PolF32x2>(h, nsteps, ncw, nstage, us_per_step);
     else if (precision == SFM_FP32F)
         rc = autotune_impl<sfm::PolF32F>(h, nsteps, ncw, nstage, us_per_step);
+    else if (precision == SFM_TF32X3 || precision == SFM_TF32)
+        rc = autotune_panel(h, panel_mode_of(precision), nsteps, ncw, nstage, us_per_step);
     else
         rc = fail(h, SFM_ERR_ARG, "sfm_autotune: unknown precision");
     h->have_init = had_init;
@@ -975,7 +1450,17 @@ extern "C" int sfm_checkpoint(sfm_handle* h, void* buf, size_t* bytes) {
     double* dU = U + n;
     const int slot = x->ck_steps % 4;                   // U^n lives in buffer n mod 4
     cudaError_t e;
-    if (x->ck_prec == SFM_FP64)
+    if (x->ck_prec == SFM_TF32X3 || x->ck_prec == SFM_TF32) {
+        // panel state (updated in place) back to the state layout
+        double *dUx = nullptr, *dDx = nullptr;
+        e = dalloc(dUx, n);
+        if (e == cudaSuccess) e = dalloc(dDx, n);
+        if (e == cudaSuccess) e = sfm::launch_from_panel(x->pb.U, dUx, x->ck_nshots, h->nstate, h->stream);
+        if (e == cudaSuccess) e = sfm::launch_from_panel(x->pb.dU, dDx, x->ck_nshots, h->nstate, h->stream);
+        if (e == cudaSuccess) e = fetch_state(dUx, dDx, n, h->stream, U, dU);
+        dfree(dUx);
+        dfree(dDx);
+    } else if (x->ck_prec == SFM_FP64)
         e = fetch_state(x->r64.U[slot], x->r64.dU, n, h->stream, U, dU);
     else if (x->ck_prec == SFM_FP32X2)
         e = fetch_state(x->r2.U[slot], x->r2.dU, n, h->stream, U, dU);

@@ -60,7 +60,80 @@ struct StepParams {
     const int4* rtab;            // [nrpairs] receiver pairs (see readout_table)
     int stage_v4;                // factored path: stage piece state with 16-byte copies
                                  // (every b a multiple of 4, FP32 storage)
+    int* ustep;                  // instability sentinel: first step whose face update
+                                 // was non-finite or beyond 1e30 (atomicMin), or NULL
 };
+
+constexpr int PANEL_NCW_MAX = 8;   // 16-shot groups (consumer warps) per panel block
+
+// Device-side description of a multi-shot panel run (panel.cu): shots in
+// groups of 16, every array FP32.  Offsets are in numbers.
+struct PanelParams {
+    int nsub, ngroups, nsteps;
+    int ncw, nstage;             // consumer warps (groups per task), ring stages
+    int bmax, rpmax;             // widest block, most receiver pairs of one subdomain
+    long long nstate, nmail;     // numbers per shot in the state and in the face data
+    const int* task_ptr;         // [grid+1] tasks of each block
+    const int4* task;            // {subdomain, first group, groups, b | k << 8}
+    const long long* coef_off;   // [nsub] first padded factor tile of the subdomain
+    const float* coef;
+    const long long* state_off;  // [nsub] (numbers per shot)
+    const long long* mail_off;   // [nsub]
+    const int4* frow;            // face rows (face_rows)
+    const float* H;
+    const long long* src_off;    // [ngroups*nsub] source panels of a unit, -1 if none
+    const float* src;
+    const float* wavelet;        // [ngroups*16][nsteps]
+    const int* sub_rp_ptr;       // [nsub+1] receiver pairs of each subdomain ...
+    const int* sub_rp;           // ... as pair indices
+    const long long* rp_off;     // [nrpairs] start of the pair's k*b row
+    const float* rrows;
+    int nrpairs;
+    float* partial;              // [ngroups][nsteps+1][nrpairs][16]
+    float* U;                    // [ngroups][nstate][16]
+    float* dU;
+    float* mail0;
+    float* mail1;
+    float dt2;
+    unsigned int* bar;
+    int* err;
+    unsigned long long timeout_ns;
+    int skip_arrive;
+    int* ustep;                  // instability sentinel (as StepParams::ustep)
+};
+
+// panel launchers (panel.cu); mode 1 = 1xTF32, 3 = 3xTF32 products
+size_t panel_smem_bytes(int ncw, int nstage, int bmax, int rpmax);
+int panel_max_grid(int mode, int ncw, size_t smem, int* grid_out);
+cudaError_t launch_panel(int mode, const PanelParams& p, int grid, cudaStream_t st);
+// LPT assignment of the tasks (subdomain, group chunk of at most ncw groups)
+// to `grid` blocks by estimated cost
+void build_panel_tasks(int nsub, int ngroups, const int* k_sub, const int* b_sub, int ncw,
+                       int grid, std::vector<int>& ptr, std::vector<int4>& tasks);
+// 64-float factor tiles -> 72-float padded tiles
+cudaError_t launch_pad_tiles(const float* in, float* out, long long ntiles, cudaStream_t st);
+// FP64 [nshots][n] -> FP32 panels [ngroups][n][16] (padded shots zero)
+cudaError_t launch_to_panel(const double* in, float* out, int nshots, long long n, cudaStream_t st);
+// FP32 panels -> FP64 [nshots][n]
+cudaError_t launch_from_panel(const float* in, double* out, int nshots, long long n, cudaStream_t st);
+// source rows of (shot, subdomain) pairs into their unit's panels:
+// rows[off64[i] .. + len[i]) go to column dst[i] % 16 of out + dst[i] - dst[i] % 16
+cudaError_t launch_src_panels(const double* rows, const long long* off64, const long long* dst,
+                              const int* len, int npairs, float* out, cudaStream_t st);
+// traces[q][r][n] = sum over the pairs of r of partial[q/16][n][pair][pos(q%16)]
+cudaError_t launch_panel_traces(const float* partial, const int* rec_ptr, const int* rec_pairs,
+                                int nshots, int nsteps, int nrec, int nrpairs, double* traces,
+                                int* bad, cudaStream_t st);
+
+// energy terms (energy.cu): out[(unit * kmax + j) * 2 + {0, 1}] =
+// {delta_j^T Gammahat_j^{-1} delta_j, Delta_j(U)^T Gamma_j Delta_j(U - delta)}
+// for U = U^{n+1}, delta = U^{n+1} - U^n in the state layout (FP64)
+cudaError_t launch_energy_terms(const double* coef, const long long* coef_off, const int* sub_b,
+                                const int* sub_k, int nsub, int kmax, int nshots, const double* U,
+                                const double* D, long long stride, const long long* state_off,
+                                double* out, cudaStream_t st);
+template <typename T>
+cudaError_t launch_state_to_f64(const T* in, double* out, size_t n, cudaStream_t st);
 
 // launchers (step.cu); P is a number policy of numeric.cuh
 template <class P>

@@ -128,7 +128,7 @@ __device__ __forceinline__ void grid_arrive(unsigned int* bar, int skip_arrive, 
     }
 }
 
-__device__ bool grid_wait(unsigned int* bar, unsigned int target, int* err,
+__device__ inline bool grid_wait(unsigned int* bar, unsigned int target, int* err,
                           unsigned long long timeout_ns, int nct) {
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
@@ -149,7 +149,7 @@ __device__ bool grid_wait(unsigned int* bar, unsigned int target, int* err,
     return s_ok != 0;
 }
 
-__device__ bool grid_barrier(unsigned int* bar, unsigned int target, int* err,
+__device__ inline bool grid_barrier(unsigned int* bar, unsigned int target, int* err,
                              unsigned long long timeout_ns, int skip_arrive, int nct) {
     grid_arrive(bar, skip_arrive, nct);
     return grid_wait(bar, target, err, timeout_ns, nct);
@@ -759,7 +759,14 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
                 for (int c = 0; c < m; ++c) P::fma(acc, P::ld(H + c * m), v[c]);
                 const C d = P::add(P::ld(p.dU + so + t), P::mul(dt2, P::get(acc)));
                 P::st(p.dU + so + t, d);
-                P::st(Unxt + so + t, P::add(P::ld(Ucur + so + t), d));
+                const C un = P::add(P::ld(Ucur + so + t), d);
+                P::st(Unxt + so + t, un);
+                if (!P::sane(un)) {
+                    // unstable (time step above the CFL limit): every block
+                    // leaves at the next device-wide barrier
+                    if (p.ustep) atomicMin(p.ustep, n);
+                    atomicCAS(p.err, 0, (int)SFM_ERR_UNSTABLE);
+                }
             }
         }
         pre = false;

@@ -28,8 +28,12 @@ SFM_FP64 = 0
 SFM_FP32 = 1
 SFM_FP32X2 = 2
 SFM_FP32F = 3
+SFM_TF32X3 = 4
+SFM_TF32 = 5
+SFM_BF16 = 6
 
 SFM_DEVICE_PTR = 1
+SFM_ENERGY = 2
 
 # every symbol include/sfm.h declares
 EXPORTS = ["sfm_create", "sfm_destroy", "sfm_last_error", "sfm_set_stream", "sfm_set_topology",
@@ -37,13 +41,19 @@ EXPORTS = ["sfm_create", "sfm_destroy", "sfm_last_error", "sfm_set_stream", "sfm
            "sfm_run", "sfm_cfl_dt", "sfm_last_launches", "sfm_debug_set", "sfm_set_model",
            "sfm_build_roms", "sfm_project_sources", "sfm_project_receivers", "sfm_free_build", "sfm_run_static",
            "sfm_autotune", "sfm_set_initial", "sfm_plan_pieces", "sfm_usable_depths",
-           "sfm_cut_depth", "sfm_checkpoint", "sfm_restore"]
+           "sfm_cut_depth", "sfm_checkpoint", "sfm_restore", "sfm_run_report"]
 
 
 class sfm_build_report(C.Structure):
     _fields_ = [("seconds", C.c_double), ("cg_iterations_max", C.c_int),
                 ("cg_residual_max", C.c_double), ("krylov_min_ratio", C.c_double),
                 ("nclasses", C.c_int), ("nregularized", C.c_int)]
+
+
+class sfm_run_info(C.Structure):
+    _fields_ = [("precision", C.c_int), ("nsteps", C.c_int), ("nshots", C.c_int),
+                ("launches", C.c_int), ("kernel_ms", C.c_double), ("total_ms", C.c_double),
+                ("status", C.c_int), ("unstable_step", C.c_int), ("energy", C.c_int)]
 
 
 class SfmError(RuntimeError):
@@ -97,6 +107,7 @@ def load(path=LIB_PATH):
         "sfm_cut_depth": (_i, [_p, C.c_double, _ip, _i, _ip]),
         "sfm_checkpoint": (_i, [_p, _p, C.POINTER(C.c_size_t)]),
         "sfm_restore": (_i, [_p, _p, C.c_size_t]),
+        "sfm_run_report": (_i, [_p, C.POINTER(sfm_run_info), _dp, _i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -187,22 +198,39 @@ def sfm_set_receivers(h, nrec, pair_rec, pair_sub, rows):
     _check(h, load().sfm_set_receivers(h, int(nrec), len(a), ap, bp, rp))
 
 
-def sfm_run(h, precision, dt, nsteps, wavelet, nshots, nrec, traces=None, device_ptrs=None):
+def sfm_run(h, precision, dt, nsteps, wavelet, nshots, nrec, traces=None, device_ptrs=None,
+            energy=False):
     """Step the coupled ROMs.  Host form: ``wavelet`` is a [nshots, nsteps]
     array and the traces [nshots, nrec, nsteps+1] are returned.  Device form:
     ``device_ptrs=(wavelet_ptr, traces_ptr)`` (FP64 device buffers).
+    ``energy``: also evaluate the discrete energy (see sfm_run_report).
     Returns ``(traces, kernel_ms)``."""
     ms = C.c_double(0.0)
+    extra = SFM_ENERGY if energy else 0
     if device_ptrs is not None:
         wp, tp = device_ptrs
         _check(h, load().sfm_run(h, int(precision), float(dt), int(nsteps), _p(int(wp)),
-                                 _p(int(tp)), SFM_DEVICE_PTR, C.byref(ms)))
+                                 _p(int(tp)), SFM_DEVICE_PTR | extra, C.byref(ms)))
         return None, ms.value
     w, _ = _darr(np.asarray(wavelet).reshape(nshots, nsteps))
     out = np.empty((nshots, nrec, nsteps + 1)) if traces is None else traces
     _check(h, load().sfm_run(h, int(precision), float(dt), int(nsteps),
-                             _p(w.ctypes.data), _p(out.ctypes.data), 0, C.byref(ms)))
+                             _p(w.ctypes.data), _p(out.ctypes.data), extra, C.byref(ms)))
     return out, ms.value
+
+
+def sfm_run_report(h):
+    """Report of the last sfm_run: a dict of the sfm_run_info fields, plus
+    ``energy_start``/``energy_end`` arrays (per shot) when it evaluated them."""
+    info = sfm_run_info()
+    _check(h, load().sfm_run_report(h, C.byref(info), None, 0))
+    out = {name: getattr(info, name) for name, _ in sfm_run_info._fields_}
+    if info.energy:
+        e = np.zeros(2 * info.nshots)
+        _check(h, load().sfm_run_report(h, C.byref(info), e.ctypes.data_as(_dp), e.size))
+        out["energy_start"] = e[:info.nshots].copy()
+        out["energy_end"] = e[info.nshots:].copy()
+    return out
 
 
 def sfm_checkpoint(h):
