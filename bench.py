@@ -53,12 +53,18 @@ def parse():
     ap.add_argument("--precision", default="auto",
                     choices=["auto", "fp32f", "tf32x3", "tf32", "fp32", "fp32x2", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the batched config-3 object of the headline line")
     ap.add_argument("--cpu-sample-steps", type=int, default=600)
-    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "paper"],
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "paper", "surrogate"],
                     help="cfg2: 192^3 cells, 512 subdomains, 1 shot (the headline); "
                          "cfg3: 256x256x128 cells, uneven subdomains, 64 shots; "
                          "paper: the 7x7x3 unit-cube layout of the paper's experiment at "
-                         "m = 10, k = 4, t in [0, 12.5]")
+                         "m = 10, k = 4, t in [0, 12.5]; surrogate: the learned surrogate "
+                         "trained and judged on 24^3 blocks (m = 8, k = 16)")
+    ap.add_argument("--sur-train", type=int, default=2000, help="surrogate workload: training blocks")
+    ap.add_argument("--sur-test", type=int, default=200, help="surrogate workload: held-out blocks")
+    ap.add_argument("--sur-epochs", type=int, default=30)
     ap.add_argument("--shape", default=None,
                     help="fixed stepping block shape 'warps,stages' instead of the autotuner's")
     return ap.parse_args()
@@ -259,6 +265,149 @@ def reference_arm(args, rank, world):
 
 # ---------------------------------------------------------------------------
 
+MODES = ("fp32f", "tf32x3", "tf32", "fp32", "fp32x2")
+DTYPE = {"fp32f": "f32", "tf32x3": "tf32x3", "tf32": "tf32", "fp32": "f32", "fp32x2": "f32x2",
+         "fp64": "f64"}
+WORD = {"fp32f": 4, "tf32x3": 4, "tf32": 4, "fp32": 4, "fp32x2": 8, "fp64": 8}
+
+
+def build_workload(sfm, h, p, workload):
+    """Offline stage on the GPU (not timed by the metric): ROMs, projections,
+    depth cut (config 3), CFL step.  Returns (dt, nsteps, dt_fine, report,
+    depth_cut, build seconds)."""
+    t0 = time.perf_counter()
+    sfm.sfm_set_model(h, p.c, p.h, p.xcuts, p.ycuts, p.zcuts)
+    rep = sfm.sfm_build_roms(h, p.m_sub, p.k_sub, p.sigma)
+    sfm.sfm_project_sources(h, p.src_xyz, p.src_width)
+    sfm.sfm_project_receivers(h, p.rec_xyz)
+    depth_cut = None
+    if workload == "cfg3":
+        # the deepest fractions of this workload run past FP64's range: keep
+        # each subdomain's usable depth (the rest of the run uses it)
+        depth, ncut = sfm.sfm_cut_depth(h, p.nsub, 1e-13)
+        depth_cut = {"tau": 1e-13, "levels_cut": int(ncut),
+                     "subdomains_cut": int((depth < p.k_sub).sum())}
+        p.k_sub = depth.astype(p.k_sub.dtype)
+    lam, dtc = sfm.sfm_cfl_dt(h, 1000)
+    sfm.sfm_free_build(h)              # the Krylov bases are not needed any more
+    build_s = time.perf_counter() - t0
+    dt = p.dt_safety * dtc
+    nsteps = p.nsteps if p.nsteps else int(np.ceil(p.meta["t_end"] / dt))
+    return dt, nsteps, fine_dt(p), rep, depth_cut, build_s
+
+
+def measure_workload(sfm, torch, h, p, args, dt, nsteps, stream, local, dist, world, warmup, steps,
+                     e2e_runs, force=None, also=()):
+    """Precision gate, block shape, timed runs (device events, L2 flushed
+    between runs, clocks sampled) and the end-to-end rate of one workload.
+    ``also``: further modes timed beside the chosen one (reported, not
+    chosen)."""
+    nshots, nrec = p.nshots, p.nrec
+    wav = torch.tensor(inputs.wavelet_samples(p, dt, nsteps), dtype=torch.float64, device="cuda")
+    tr = torch.empty((nshots, nrec, nsteps + 1), dtype=torch.float64, device="cuda")
+    modes = {"fp32f": sfm.SFM_FP32F, "tf32x3": sfm.SFM_TF32X3, "tf32": sfm.SFM_TF32,
+             "fp32": sfm.SFM_FP32, "fp32x2": sfm.SFM_FP32X2, "fp64": sfm.SFM_FP64}
+
+    def run(prec):
+        _, ms = sfm.sfm_run(h, prec, dt, nsteps, None, nshots, nrec,
+                            device_ptrs=(wav.data_ptr(), tr.data_ptr()))
+        return ms
+
+    # FP64 reference of the same ROMs, then the precision gate
+    run(sfm.SFM_FP64)
+    torch.cuda.synchronize()
+    ref = tr.cpu().numpy()
+    errors = {"fp64": 0.0}
+    for name in MODES:
+        try:
+            run(modes[name])
+            torch.cuda.synchronize()
+            errors[name] = rel_l2(tr.cpu().numpy(), ref)
+        except sfm.SfmError as e:
+            errors[name] = float("inf") if e.code == sfm.SFM_ERR_UNSTABLE else None
+    if force:
+        chosen = force
+    else:
+        chosen = next(n for n in ("fp32f", "tf32x3", "fp32", "fp32x2", "fp64")
+                      if errors.get(n) is not None and errors[n] <= GATE)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    timed = {}
+    for name in [chosen] + [a for a in also if a != chosen]:
+        prec = modes[name]
+        if args.shape:
+            fixed = [int(v) for v in args.shape.split(",")]
+            tune = (fixed[0], fixed[1], None)
+            sfm.sfm_debug_set(h, 3, fixed[0])
+            sfm.sfm_debug_set(h, 4, fixed[1])
+        else:
+            tune = sfm.sfm_autotune(h, prec, 200 if nsteps >= 200 else nsteps)
+        for _ in range(warmup):
+            run(prec)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        kern_ms = []
+        with Clocks(local) as clk:
+            torch.cuda.synchronize()
+            wall0 = time.perf_counter()
+            for i in range(steps):
+                flush.fill_(float(i))
+                ev[i][0].record(stream)
+                kern_ms.append(run(prec))
+                ev[i][1].record(stream)
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            wall = time.perf_counter() - wall0
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        timed[name] = {"ms": max_over_ranks(statistics.mean(step_ms), dist, "cuda"),
+                       "kernel_ms": statistics.mean(kern_ms), "launches": sfm.sfm_last_launches(h) * steps,
+                       "clocks": clk.summary(), "wall": wall,
+                       "block_shape": {"consumer_warps": tune[0], "ring_stages": tune[1],
+                                       "probe_us_per_time_step": tune[2]}}
+    # end to end through the public API with host buffers (H2D of the
+    # wavelet and D2H of the traces inside the timed region)
+    host_w = inputs.wavelet_samples(p, dt, nsteps)
+    host_tr = np.empty((nshots, nrec, nsteps + 1))
+    e2e_t = []
+    for _ in range(max(1, e2e_runs)):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        sfm.sfm_run(h, modes[chosen], dt, nsteps, host_w, nshots, nrec, traces=host_tr)
+        e2e_t.append(time.perf_counter() - t1)
+    return chosen, errors, timed, statistics.mean(e2e_t), host_w.nbytes, host_tr.nbytes
+
+
+def roofline_of(p, name, t, nsteps, pk, pk_kind, traffic):
+    word = WORD[name]
+    bytes_step = algorithmic_bytes_per_step(p, p.nshots, receiver_row_numbers(p), word)
+    achieved = bytes_step * nsteps / (t["kernel_ms"] * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
+            "peak_source": f"{pk_kind} HBM copy",
+            "kernel": "panel_kernel" if name in ("tf32x3", "tf32") else "step_kernel",
+            "kernel_ms": t["kernel_ms"], "bytes_per_time_step": bytes_step}
+
+
+def cpu_baseline_run(threads, sample_steps):
+    """The oracle's stepping on a bounded sample, in a child process whose
+    BLAS/OpenMP pools are set to ``threads`` before NumPy loads (the child
+    never touches the GPU).  Returns (value, wall seconds, cores used)."""
+    env = dict(os.environ)
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[var] = str(threads)
+    code = ("import json, bench; p, rs, dt, dtf = bench.oracle_sample({n}); "
+            "v, w, c = bench.time_oracle(p, rs, dt, dtf, {n}); print(json.dumps([v, w, c]))").format(n=sample_steps)
+    r = subprocess.run([sys.executable, "-c", code], env=env, cwd=ROOT, capture_output=True, text=True,
+                       timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(f"oracle baseline failed: {r.stderr[-500:]}")
+    v, w, c = json.loads(r.stdout.strip().splitlines()[-1])
+    return v, w, c
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -276,168 +425,219 @@ def main():
         dist.init_process_group("nccl")
     from paper_1406_6923_gb300 import sfm
 
-    if args.workload == "cfg2":
-        p = inputs.config2()
-    elif args.workload == "cfg3":
-        p = inputs.config3()
-    else:
-        p = inputs.paper_layout(m=10, k=4)      # the widest blocks the stepping takes
+    if args.workload == "surrogate":
+        surrogate_experiment(sfm, torch, args)
+        return
+    makers = {"cfg2": inputs.config2, "cfg3": inputs.config3,
+              "paper": lambda: inputs.paper_layout(m=10, k=4)}   # the widest blocks the stepping takes
+    p = makers[args.workload]()
     stream = torch.cuda.current_stream()
     h = sfm.sfm_create(local)
     sfm.sfm_set_stream(h, stream.cuda_stream)
-    t0 = time.perf_counter()
-    sfm.sfm_set_model(h, p.c, p.h, p.xcuts, p.ycuts, p.zcuts)
-    rep = sfm.sfm_build_roms(h, p.m_sub, p.k_sub, p.sigma)
-    sfm.sfm_project_sources(h, p.src_xyz, p.src_width)
-    sfm.sfm_project_receivers(h, p.rec_xyz)
-    depth_cut = None
-    if args.workload == "cfg3":
-        # the deepest fractions of this workload run past FP64's range: keep
-        # each subdomain's usable depth (the rest of the run uses it)
-        depth, ncut = sfm.sfm_cut_depth(h, p.nsub, 1e-13)
-        depth_cut = {"tau": 1e-13, "levels_cut": int(ncut),
-                     "subdomains_cut": int((depth < p.k_sub).sum())}
-        p.k_sub = depth.astype(p.k_sub.dtype)
-    lam, dtc = sfm.sfm_cfl_dt(h, 1000)
-    sfm.sfm_free_build(h)              # the Krylov bases are not needed any more
-    build_s = time.perf_counter() - t0
-    dt = p.dt_safety * dtc
+    dt, nsteps, dtf, rep, depth_cut, build_s = build_workload(sfm, h, p, args.workload)
     if args.nsteps:
         nsteps = args.nsteps
-    elif p.nsteps:
-        nsteps = p.nsteps
-    else:                              # the paper layout: its time window
-        nsteps = int(np.ceil(p.meta["t_end"] / dt))
-    dtf = fine_dt(p)
-    nshots, nrec = p.nshots, p.nrec
-    if args.shape:
-        fixed = [int(v) for v in args.shape.split(",")]
-        sfm.sfm_debug_set(h, 3, fixed[0])
-        sfm.sfm_debug_set(h, 4, fixed[1])
-    wav = torch.tensor(inputs.wavelet_samples(p, dt, nsteps), dtype=torch.float64, device="cuda")
-    tr = torch.empty((nshots, nrec, nsteps + 1), dtype=torch.float64, device="cuda")
-
-    def run(prec):
-        _, ms = sfm.sfm_run(h, prec, dt, nsteps, None, nshots, nrec,
-                            device_ptrs=(wav.data_ptr(), tr.data_ptr()))
-        return ms
-
-    # FP64 reference of the same ROMs, then the precision gate
-    run(sfm.SFM_FP64)
-    torch.cuda.synchronize()
-    ref = tr.cpu().numpy()
-    modes = {"fp32f": sfm.SFM_FP32F, "tf32x3": sfm.SFM_TF32X3, "tf32": sfm.SFM_TF32,
-             "fp32": sfm.SFM_FP32, "fp32x2": sfm.SFM_FP32X2, "fp64": sfm.SFM_FP64}
-    errors = {"fp64": 0.0}
-    for name in ("fp32f", "tf32x3", "tf32", "fp32", "fp32x2"):
-        try:
-            run(modes[name])
-            torch.cuda.synchronize()
-            errors[name] = rel_l2(tr.cpu().numpy(), ref)
-        except sfm.SfmError as e:
-            errors[name] = float("inf") if e.code == sfm.SFM_ERR_UNSTABLE else None
-    if args.precision == "auto":
-        chosen = next(n for n in ("fp32f", "tf32x3", "fp32", "fp32x2", "fp64")
-                      if errors.get(n) is not None and errors[n] <= GATE)
-    else:
-        chosen = args.precision
-    prec = modes[chosen]
-    # block shape of the stepping kernel, picked by the library's autotuner
-    # (zero-source probes, outside the timed region)
-    if args.shape:
-        tune_ncw, tune_nst, tune_us = fixed[0], fixed[1], None
-    else:
-        tune_ncw, tune_nst, tune_us = sfm.sfm_autotune(h, prec, 200)
-
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
-    for _ in range(args.warmup):
-        run(prec)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    kern_ms = []
-    with Clocks(local) as clk:
-        torch.cuda.synchronize()
-        wall0 = time.perf_counter()
-        for i in range(args.steps):
-            flush.fill_(float(i))
-            ev[i][0].record(stream)
-            kern_ms.append(run(prec))
-            ev[i][1].record(stream)
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        wall = time.perf_counter() - wall0
-    launches = sfm.sfm_last_launches(h) * args.steps
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = max_over_ranks(statistics.mean(step_ms), dist, "cuda")
+    chosen, errors, timed, e2e_s, h2d, d2h = measure_workload(
+        sfm, torch, h, p, args, dt, nsteps, stream, local, dist, world, args.warmup, args.steps, args.steps,
+        force=None if args.precision == "auto" else args.precision)
+    sfm.sfm_destroy(h)
+    t = timed[chosen]
+    ms = t["ms"]
+    nshots = p.nshots
     ncell = p.nx * p.ny * p.nz
     bw = face_modes(p).sum(axis=1)
     widths = int(bw[0]) if bw.min() == bw.max() else [int(bw.min()), int(bw.max())]
     kk = np.asarray(p.k_sub)
     levels = int(kk[0]) if kk.min() == kk.max() else [int(kk.min()), int(kk.max())]
     value = whole_job_rate(ncell * nsteps * (dt / dtf) * nshots, ms, world)
-
-    # end to end through the public API with host buffers (H2D of the
-    # wavelet and D2H of the traces inside the timed region)
-    host_w = inputs.wavelet_samples(p, dt, nsteps)
-    host_tr = np.empty((nshots, nrec, nsteps + 1))
-    e2e_t = []
-    for i in range(max(1, args.steps)):
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        sfm.sfm_run(h, prec, dt, nsteps, host_w, nshots, nrec, traces=host_tr)
-        e2e_t.append(time.perf_counter() - t1)
-    e2e_val = ncell * nsteps * (dt / dtf) * nshots / statistics.mean(e2e_t) * world
-
-    # roofline of the persistent stepping kernel
+    e2e_val = ncell * nsteps * (dt / dtf) * nshots / e2e_s * world
     pk, pk_kind = peaks()
-    word = {"fp32f": 4, "tf32x3": 4, "tf32": 4, "fp32": 4, "fp32x2": 8, "fp64": 8}[chosen]
-    bytes_step = algorithmic_bytes_per_step(p, nshots, receiver_row_numbers(p), word)
-    kms = statistics.mean(kern_ms)
-    achieved = bytes_step * nsteps / (kms * 1e-3) / 1e9
-    traffic = read_traffic() if args.workload == "cfg2" else None
-    roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
-            "peak_source": f"{pk_kind} HBM copy", "kernel": "step_kernel",
-            "kernel_ms": kms, "bytes_per_time_step": bytes_step}
+    traffic = read_traffic() if (args.workload == "cfg2" and chosen == "fp32f") else None
+    roof = roofline_of(p, chosen, t, nsteps, pk, pk_kind, traffic)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "cfg2":
-        po, rs, dto, dtfo = oracle_sample(args.cpu_sample_steps)
-        v, wall_c, cores = time_oracle(po, rs, dto, dtfo, args.cpu_sample_steps)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+        ncores = os.cpu_count() or 1
+        v_all, w_all, c_all = cpu_baseline_run(ncores, args.cpu_sample_steps)
+        v_one, w_one, c_one = cpu_baseline_run(1, args.cpu_sample_steps)
+        cpu = {"value": v_all, "unit": UNIT, "cores": c_all, "kind": "oracle",
                "sample": (f"config-2 stepping, {args.cpu_sample_steps} of its time steps, "
-                          f"oracle-built ROMs of a uniform 3000 m/s medium on the same grid, "
-                          f"{wall_c:.1f} s")}
+                          f"oracle-built ROMs of a uniform 3000 m/s medium on the same grid "
+                          f"(identical stepping cost), BLAS/OpenMP pools of {ncores} threads "
+                          f"on a host of {ncores} cores, {w_all:.1f} s"),
+               "nproc": ncores, "one_core": {"value": v_one, "cores": c_one, "seconds": w_one}}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": {"fp32f": "f32", "tf32x3": "tf32x3", "tf32": "tf32", "fp32": "f32",
-                     "fp32x2": "f32x2", "fp64": "f64"}[chosen],
-           "data": "synthetic",
+           "vs_baseline": None, "dtype": DTYPE[chosen], "data": "synthetic",
            "config": {"workload": p.name, "cells": ncell, "subdomains": p.nsub,
                       "b": widths, "k": levels,
-                      "shots": nshots, "receivers": nrec, "time_steps": nsteps,
+                      "shots": nshots, "receivers": p.nrec, "time_steps": nsteps,
                       "precision": chosen, "trace_err_vs_fp64": errors,
                       "dt": dt, "dt_fine": dtf, "dt_ratio": dt / dtf,
                       "conservative_value": ncell * nsteps * nshots / (ms * 1e-3) * world,
                       "l2": "256 MB buffer written between timed iterations",
                       "parallelism": "replicas" if world > 1 else "single GPU",
                       "offline_build_s": build_s, "build": rep, "depth_cut": depth_cut,
-                      "block_shape": {"consumer_warps": tune_ncw, "ring_stages": tune_nst,
-                                      "probe_us_per_time_step": tune_us}},
+                      "block_shape": t["block_shape"]},
            "roofline": roof, "cpu_baseline": cpu,
-           "e2e": {"value": e2e_val, "unit": UNIT,
-                   "h2d_bytes_per_step": int(host_w.nbytes), "d2h_bytes_per_step": int(host_tr.nbytes)},
-           "gpu_launches": launches, "clocks": clk.summary(), "wall_s_timed": wall}
+           "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+           "gpu_launches": t["launches"], "clocks": t["clocks"], "wall_s_timed": t["wall"]}
+
+    if args.workload == "cfg2" and world == 1 and not args.no_extra:
+        out["extra"] = {"cfg3": batched_extra(sfm, torch, args, local, pk, pk_kind)}
     if rank == 0:
         print(json.dumps(out), flush=True)
-    sfm.sfm_destroy(h)
     if dist:
         dist.destroy_process_group()
+
+
+def batched_extra(sfm, torch, args, local, pk, pk_kind):
+    """The batched workload (256 x 256 x 128 cells, 495 uneven subdomains,
+    64 shots, 3000 steps) measured beside the headline: its gated precision
+    and the multi-shot tensor-core panel mode (SFM_TF32X3), each with 3
+    warm-up and 2 timed runs, L2 flushed between runs."""
+    p = inputs.config3()
+    stream = torch.cuda.current_stream()
+    h = sfm.sfm_create(local)
+    sfm.sfm_set_stream(h, stream.cuda_stream)
+    dt, nsteps, dtf, rep, depth_cut, build_s = build_workload(sfm, h, p, "cfg3")
+    chosen, errors, timed, e2e_s, h2d, d2h = measure_workload(
+        sfm, torch, h, p, args, dt, nsteps, stream, local, None, 1, 3, 2, 1, also=("tf32x3",))
+    sfm.sfm_destroy(h)
+    ncell = p.nx * p.ny * p.nz
+    rate = lambda ms: ncell * nsteps * (dt / dtf) * p.nshots / (ms * 1e-3)
+    t = timed[chosen]
+    res = {"workload": p.name, "cells": ncell, "subdomains": p.nsub, "shots": p.nshots,
+           "receivers": p.nrec, "time_steps": nsteps, "depth_cut": depth_cut, "offline_build_s": build_s,
+           "precision": chosen, "value": rate(t["ms"]), "unit": UNIT, "ms_per_step": t["ms"],
+           "trace_err_vs_fp64": errors, "roofline": roofline_of(p, chosen, t, nsteps, pk, pk_kind, None),
+           "block_shape": t["block_shape"], "clocks": t["clocks"],
+           "e2e": {"value": ncell * nsteps * (dt / dtf) * p.nshots / e2e_s, "unit": UNIT,
+                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}}
+    if "tf32x3" in timed and chosen != "tf32x3":
+        tp = timed["tf32x3"]
+        err = errors.get("tf32x3")
+        res["tf32x3_panel"] = {"value": rate(tp["ms"]), "ms_per_step": tp["ms"], "trace_err_vs_fp64": err,
+                               "passes_gate": err is not None and err <= GATE,
+                               "roofline": roofline_of(p, "tf32x3", tp, nsteps, pk, pk_kind, None),
+                               "block_shape": tp["block_shape"], "clocks": tp["clocks"]}
+    return res
+
+
+def ntd_frequencies(f_peak, count=16, eta_hz=4.0, band=2.5):
+    """lambda_i = (eta + i w_i)^2, w_i = 2 pi f_i, f_i evenly spaced in
+    (0, band * f_peak], eta = 2 pi eta_hz: the frequencies the surrogate's
+    NtD maps are judged at."""
+    f = band * f_peak * np.arange(1, count + 1) / count
+    return (2 * np.pi * eta_hz + 2j * np.pi * f) ** 2
+
+
+def surrogate_experiment(sfm, torch, args):
+    """The learned surrogate at the size of the surrogate workload (24^3-cell
+    blocks, m = 8, k = 16): exact ROMs of the training and test blocks from
+    the GPU builder, the decoder fit, FP32 training on the GPU, the NtD-map
+    error at 16 frequencies of the BF16 network on the held-out blocks (and
+    of the decoder's mean ROM, the baseline), then the offline stage of a
+    model tiled by held-out blocks with the surrogate and exact fallback at
+    several tolerances against the plain build: time per block and trace
+    error of the FP64 stepping.  Prints one JSON line."""
+    from paper_1406_6923_gb300 import surrogate as sur
+    n, m, k, f_peak = 24, 8, 16, 20.0
+    b, code = 6 * m, 64
+    sigma = inputs.default_sigma(f_peak, 8.0)
+    ntr, nte = args.sur_train, args.sur_test
+    blocks = inputs.surrogate_blocks(ntr + nte, n=n)
+    h = sfm.sfm_create(0)
+    t0 = time.perf_counter()
+    sets, per_block = sur.build_sets(h, blocks, 10.0, m, k, sigma)
+    sfm.sfm_destroy(h)
+    build_wall = time.perf_counter() - t0
+    dev = "cuda"
+    nb = len(blocks)
+    sets_d = torch.tensor(sets.reshape(nb, -1), device=dev)
+    raw = torch.empty((nb, sfm.raw_size(b, k)), dtype=torch.float64, device=dev)
+    sfm.sfm_raw_encode(0, nb, b, k, sets_d.data_ptr(), raw.data_ptr())
+    net = sfm.sfm_net_create(0, n, 16, 32, 64, 1024, code, 1)
+    nparams = sfm.sfm_net_params(net).size
+    codes = torch.empty((ntr, code), dtype=torch.float32, device=dev)
+    t1 = time.perf_counter()
+    sfm.sfm_net_fit_decoder(net, b, k, raw.data_ptr(), ntr, iters=4, seed=7, codes_ptr=codes.data_ptr())
+    fit_s = time.perf_counter() - t1
+    c = torch.tensor(np.asarray(blocks, np.float32), device=dev)
+    t1 = time.perf_counter()
+    losses = sur.train(torch, net, c[:ntr].contiguous(), codes, epochs=args.sur_epochs, batch=32, lr=1e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    lams = ntd_frequencies(f_peak)
+    exact = sets_d[ntr:].contiguous()
+    pred = sur.predict_sets(torch, net, code, c[ntr:].contiguous(), exact, bf16=True)
+    e_net = sfm.sfm_ntd_error(0, nte, b, k, pred.data_ptr(), exact.data_ptr(), lams).max(axis=1)
+    zero = torch.zeros((nte, code), dtype=torch.float32, device=dev)
+    mean = exact.clone()
+    sfm.sfm_net_decode(net, zero.data_ptr(), nte, mean.data_ptr())
+    e_mean = sfm.sfm_ntd_error(0, nte, b, k, mean.data_ptr(), exact.data_ptr(), lams).max(axis=1)
+    # the offline stage of a model of held-out blocks: plain vs surrogate
+    side = 4
+    idx = np.arange(ntr, ntr + side ** 3) % nb
+    cm, xc, yc, zc, order = sur.tile_blocks(blocks[idx])
+    nsub = len(order)
+    msub, ksub = np.full(nsub, m), np.full(nsub, k)
+    centre = lambda i, j, l: [(i + 0.5) * n * 10.0, (j + 0.5) * n * 10.0, (l + 0.5) * n * 10.0]
+    src = np.array([centre(1, 1, 1)])
+    rec = np.array([centre(i, 2, 2) for i in range(side)])
+    exact_mask = np.zeros(nsub, dtype=np.int32)
+    for x in np.concatenate([src, rec]):
+        i, j, l = (int(v // (n * 10.0)) for v in x)
+        exact_mask[i + side * (j + side * l)] = 1
+    hh = sfm.sfm_create(0)
+    sfm.sfm_set_model(hh, cm, 10.0, xc, yc, zc)
+    tp = time.perf_counter()
+    sfm.sfm_build_roms(hh, msub, ksub, sigma)
+    plain_s = time.perf_counter() - tp
+    sfm.sfm_project_sources(hh, src, 10.0)
+    sfm.sfm_project_receivers(hh, rec)
+    lam_max, dtc = sfm.sfm_cfl_dt(hh, 1000)
+    dt = 0.9 * dtc
+    nst = 600
+    w = inputs.ricker(np.arange(nst) * dt, f_peak)[None]
+    ref, _ = sfm.sfm_run(hh, sfm.SFM_FP64, dt, nst, w, 1, len(rec))
+    tolerances = []
+    for tol in (1e-3, 1e-2, 1e-1, float("inf")):
+        ts = time.perf_counter()
+        srep, _ = sfm.sfm_build_roms_surrogate(hh, net, msub, ksub, sigma, tol, exact=exact_mask)
+        wall = time.perf_counter() - ts
+        sfm.sfm_project_sources(hh, src, 10.0)
+        sfm.sfm_project_receivers(hh, rec)
+        row = {"nt_tol": tol, "accepted": srep["accepted"], "fallback": srep["fallback"],
+               "served": srep["eligible"], "sigma_err_median": srep["sigma_err_median"],
+               "build_s": wall, "build_s_per_block": wall / nsub,
+               "surrogate_pass_s": srep["seconds_surrogate"], "exact_pass_s": srep["seconds_exact"]}
+        try:
+            got, _ = sfm.sfm_run(hh, sfm.SFM_FP64, dt, nst, w, 1, len(rec))
+            row["trace_err_vs_plain"] = rel_l2(got, ref)
+        except sfm.SfmError as e:
+            row["trace_err_vs_plain"] = None
+            row["run_error"] = str(e)
+        tolerances.append(row)
+    sfm.sfm_destroy(hh)
+    sfm.sfm_net_destroy(net)
+    out = {"workload": "surrogate_24c_m8_k16", "train_blocks": ntr, "test_blocks": nte,
+           "network": {"params": int(nparams), "channels": [16, 32, 64], "hidden": 1024, "code": code,
+                       "train": "FP32, Adam 1e-3, batch 32", "epochs": args.sur_epochs,
+                       "loss_first_epoch": losses[0], "loss_last_epoch": losses[-1],
+                       "train_s": train_s, "inference": "BF16 weights and activations, FP32 accumulation"},
+           "builder": {"blocks": nb, "wall_s": build_wall, "blocks_per_s": nb / build_wall,
+                       "s_per_block_in_build": per_block},
+           "decoder_fit_s": fit_s,
+           "ntd_error_16_freqs": {"network_median": float(np.median(e_net)),
+                                  "network_p90": float(np.percentile(e_net, 90)),
+                                  "network_max": float(e_net.max()),
+                                  "mean_rom_median": float(np.median(e_mean))},
+           "offline_stage_4x4x4": {"plain_build_s": plain_s, "plain_s_per_block": plain_s / nsub,
+                                   "exact_marked": int(exact_mask.sum()), "time_steps": nst,
+                                   "by_tolerance": tolerances}}
+    print(json.dumps(out), flush=True)
 
 
 def receiver_row_numbers(p):

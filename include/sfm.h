@@ -422,6 +422,126 @@ int sfm_run_static(int device, void* stream, int nsub, const int* k_sub, const i
                    double dt, int nsteps, const double* wavelet, double* traces);
 
 /*
+ * ---------------------------------------------------------------------------
+ * Learned surrogate of the offline stage (an extension of Algorithm 1 stage
+ * 1, Eqs. 5-13: when the velocity changes between inversion iterations, a
+ * network maps a subdomain's velocity block to its S-fraction coefficients)
+ * ---------------------------------------------------------------------------
+ * Network: input log(c / 2500 m/s) on an n^3 block of cells; three 3x3x3
+ * convolutions of stride 2 and zero padding 1 with c1, c2, c3 channels and
+ * ReLU; a dense layer of `hidden` units with ReLU; a dense layer to a code
+ * z of `code` numbers.  Parameters in the order c1 weights [c1][1][3][3][3],
+ * c1 biases, c2 weights [c2][c1][3][3][3], c2 biases, c3 weights, c3 biases,
+ * W1 [hidden][c3 * m^3] (m = the block side after three stride-2 layers;
+ * features flattened channel-major, then z, y, x), b1, W2 [code][hidden],
+ * b2.  Training is FP32 (loss: mean over the batch of the mean squared code
+ * error; Adam); inference FP32 or BF16 (BF16 weights and convolution
+ * activations, FP32 accumulation).  Device arrays are on the network's
+ * device; velocities are FP32 [batch][n][n][n] (z, y, x), codes FP32
+ * [batch][code].  Errors are reported through sfm_net_last_error.
+ */
+typedef struct sfm_net sfm_net;
+
+/* Create a network with seeded He-style initial weights (biases zero).
+ * Errors: SFM_ERR_ARG (sizes), SFM_ERR_CUDA, SFM_ERR_NOMEM. */
+int sfm_net_create(sfm_net** net, int device, int n, int c1, int c2, int c3, int hidden, int code,
+                   unsigned long long seed);
+int sfm_net_destroy(sfm_net* net);
+const char* sfm_net_last_error(const sfm_net* net);
+
+/* All parameters as one FP32 host array in the order above: set = 0 copies
+ * them out, set = 1 replaces them (and resets the Adam moments).  *count
+ * receives the parameter count; host NULL only asks for it. */
+int sfm_net_params(sfm_net* net, float* host, size_t capacity, size_t* count, int set);
+
+/* Loss of a batch of B blocks c (device) against target codes zt (device),
+ * and the gradient of every parameter by the backward pass, kept for
+ * sfm_net_adam; grad_host (host, parameter count) may be NULL. */
+int sfm_net_grad(sfm_net* net, const float* c, const float* zt, int B, float* loss, float* grad_host);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with the last gradient. */
+int sfm_net_adam(sfm_net* net, float lr);
+
+/* Codes z (device [B][code]) of B blocks c (device); bf16 selects the BF16
+ * inference pass. */
+int sfm_net_forward(sfm_net* net, const float* c, int B, float* z, int bf16);
+
+/*
+ * Decoder of the surrogate (FP64, fixed once fitted, not trained).  A set of
+ * S-fraction coefficients of width b and k >= 2 levels is 2k blocks b x b in
+ * the sfm_set_coeffs order (Gamma_1..k, Gammahat_1..k); its raw vector is,
+ * for the blocks Gamma_2..Gamma_k then Gammahat_2..Gammahat_k, the strictly
+ * lower entries of U row by row followed by log of the pivots, where the
+ * Cholesky factor of the block is L = U diag(pivots), U unit lower
+ * triangular: nraw = 2 (k-1) (b(b-1)/2 + b) numbers per set.  Every raw
+ * vector decodes to positive definite blocks L L^T, and a raw error moves a
+ * pivot by a relative factor.  Level 1 is not encoded: it has closed forms
+ * (Gammahat_1 = F^T F, Gamma_1 = Gammahat_1^{-1} F^T L F Gammahat_1^{-1}).
+ *
+ * sfm_raw_encode: raw vectors [count][nraw] (device) of count coefficient
+ *   sets (device); a pivot at or below 1e-14 of the block's largest
+ *   diagonal entry (a level semi-definite to rounding) is floored there.
+ * sfm_net_fit_decoder: the decoder of the network for (b, k): mu = the mean
+ *   of N raw targets [N][nraw] (device) and P [nraw][code], an orthonormal
+ *   basis of their leading principal subspace by randomized subspace
+ *   iteration (Halko, Martinsson and Tropp) with `iters` power passes and
+ *   Cholesky-QR orthonormalisation; codes (device FP32 [N][code], may be
+ *   NULL) receive the targets' codes P^T (raw - mu).  N >= code.
+ * sfm_net_decode: coefficient sets (device FP64, B sets) of B codes (device
+ *   FP32): levels 2..k written from mu + P z, level 1 left untouched.
+ * sfm_ntd_error: err[i][l] = |S_a - S_r|_F / |S_r|_F of two families of
+ *   count coefficient sets (device) at nlam complex lambda (host
+ *   [nlam][re, im]), S the S-fraction's transfer function (Eq. 15) by its
+ *   continued fraction Y_k = lambda Gammahat_k^{-1} + Gamma_k,
+ *   Y_j = lambda Gammahat_j^{-1} + (Gamma_j^{-1} + Y_{j+1}^{-1})^{-1},
+ *   S = Y_1^{-1}, in FP64 complex arithmetic on the device; err is host
+ *   [count][nlam].
+ * Errors: SFM_ERR_ARG, SFM_ERR_STATE (no decoder), SFM_ERR_BREAKDOWN
+ * (rank-deficient targets), SFM_ERR_CUDA, SFM_ERR_NOMEM; through
+ * sfm_net_last_error or, without a network, sfm_last_error(NULL).
+ */
+int sfm_raw_encode(int device, int count, int b, int k, const double* coef, double* raw);
+int sfm_net_fit_decoder(sfm_net* net, int b, int k, const double* raw, int N, int iters,
+                        unsigned long long seed, float* codes);
+int sfm_net_decode(sfm_net* net, const float* z, int B, double* coef);
+int sfm_ntd_error(int device, int count, int b, int k, const double* coef_a, const double* coef_r,
+                  int nlam, const double* lam, double* err);
+
+/*
+ * Offline stage with the surrogate (replacing Algorithm 1 steps 1.1-1.3 for
+ * the subdomains the network can serve, with the exact build as fallback).
+ * A subdomain is served when it is a cube of the network's n cells, has the
+ * decoder's k levels and m = b/6 modes on all six faces (its neighbours'
+ * m included), and exact[s] is 0 (exact may be NULL).  For the served
+ * subdomains, in batches on the device: level 1 from its closed forms
+ * (Gammahat_1 = F^T F, Gamma_1 = Gammahat_1^{-1} F^T L F Gammahat_1^{-1}),
+ * levels 2..k from the network (BF16 inference) and its decoder, and one
+ * block solve S(sigma) = F^T (L + sigma)^{-1} F (CG to cg_tol); a subdomain
+ * whose decoded S-fraction misses S(sigma) by more than nt_tol (relative
+ * Frobenius) falls back to the exact build, which then runs for the
+ * fallbacks and every subdomain not served (as sfm_build_roms would, with
+ * the same m_sub, k_sub, sigma and cg_tol).  Coefficients of served
+ * subdomains carry no Krylov basis: sources and receivers must not touch
+ * them (mark their subdomains exact), else sfm_project_* returns
+ * SFM_ERR_STATE.  rep (may be NULL) reports the exact build; srep (may be
+ * NULL) the surrogate pass.  Errors: as sfm_build_roms, and SFM_ERR_STATE
+ * (the network has no decoder).
+ */
+typedef struct sfm_surrogate_report {
+    int eligible;                 /* subdomains the network served             */
+    int accepted;                 /* ... whose S(sigma) passed nt_tol          */
+    int fallback;                 /* ... rebuilt exactly                       */
+    double sigma_err_median;      /* median relative S(sigma) error, served    */
+    double sigma_err_max_accepted;
+    double seconds_surrogate;     /* wall time of the surrogate pass           */
+    double seconds_exact;         /* wall time of the exact build that followed */
+} sfm_surrogate_report;
+
+int sfm_build_roms_surrogate(sfm_handle* h, sfm_net* net, const int* m_sub, const int* k_sub,
+                             double sigma, double cg_tol, double nt_tol, const int* exact,
+                             sfm_surrogate_report* srep, sfm_build_report* rep);
+
+/*
  * The stepping kernel's work partition (host logic only, no device work; no
  * counterpart in the paper): the (unit, level) sequence of nunits units,
  * unit u having k_sub[u % nsub] levels, cut into contiguous pieces for

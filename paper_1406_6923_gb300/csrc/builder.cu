@@ -230,8 +230,12 @@ extern "C" int sfm_set_model(sfm_handle* h, int nx, int ny, int nz, double hgrid
     return SFM_OK;
 }
 
-extern "C" int sfm_build_roms(sfm_handle* h, const int* m_sub, const int* k_sub, double sigma,
-                              double cg_tol, sfm_build_report* rep) {
+// The exact build (Algorithm 1 steps 1.1-1.3).  only: when not NULL, just the
+// subdomains with only[s] != 0 are built (the others keep the coefficients
+// of d_preset, a full coefficient array on the device, and have no Krylov
+// basis for the projections of step 1.4).
+static int build_impl(sfm_handle* h, const int* m_sub, const int* k_sub, double sigma, double cg_tol,
+                      sfm_build_report* rep, const std::vector<char>* only, const double* d_preset) {
     if (!h) return SFM_ERR_ARG;
     BuildState* B = bstate(h);
     if (!B || !B->d_c) return bfail(h, SFM_ERR_STATE, "sfm_build_roms: no model");
@@ -273,6 +277,10 @@ extern "C" int sfm_build_roms(sfm_handle* h, const int* m_sub, const int* k_sub,
     B->sub_class.assign(nsub, 0);
     B->sub_pos.assign(nsub, 0);
     for (int s = 0; s < nsub; ++s) {
+        if (only && !(*only)[s]) {
+            B->sub_class[s] = -1;
+            continue;
+        }
         const int ix = s % ncx, iy = (s / ncx) % ncy, iz = s / (ncx * ncy);
         std::vector<int> key = {B->xc[ix + 1] - B->xc[ix], B->yc[iy + 1] - B->yc[iy],
                                 B->zc[iz + 1] - B->zc[iz], k_sub[s]};
@@ -310,6 +318,8 @@ extern "C" int sfm_build_roms(sfm_handle* h, const int* m_sub, const int* k_sub,
     // device coefficient array in the stepping layout
     double* d_coef = nullptr;
     BCK(h, dmalloc(d_coef, (size_t)h->ncoef));
+    if (d_preset)
+        BCK(h, cudaMemcpyAsync(d_coef, d_preset, (size_t)h->ncoef * sizeof(double), cudaMemcpyDeviceToDevice, st));
 
     int* d_err = nullptr;
     double* d_ratio = nullptr;
@@ -573,6 +583,11 @@ extern "C" int sfm_build_roms(sfm_handle* h, const int* m_sub, const int* k_sub,
     return SFM_OK;
 }
 
+extern "C" int sfm_build_roms(sfm_handle* h, const int* m_sub, const int* k_sub, double sigma,
+                              double cg_tol, sfm_build_report* rep) {
+    return build_impl(h, m_sub, k_sub, sigma, cg_tol, rep, nullptr, nullptr);
+}
+
 // Point weights of a set of points for every subdomain that holds one of
 // their nodes: share M^a/M at shared nodes (Algorithm 1 step 1.4 reading).
 // kind 0: Gaussian of the given width (cut at 3 widths, normalised);
@@ -649,6 +664,10 @@ static int project_points(sfm_handle* h, int npts, const double* xyz, int kind, 
             for (int a = 0; a < (int)B->zc.size() - 1; ++a) if (B->zc[a] <= k && k <= B->zc[a + 1]) sz.push_back(a);
             for (int a : sx) for (int bq : sy) for (int cq : sz) {
                 const int s = a + ncx * (bq + ncy * cq);
+                if (B->sub_class[s] < 0)
+                    return bfail(h, SFM_ERR_STATE, "projection onto subdomain " + std::to_string(s) +
+                                                       ", whose ROM came from the surrogate (no Krylov "
+                                                       "basis): mark it exact");
                 const BClass& c = B->classes[B->sub_class[s]];
                 const int li = (i - B->xc[a]) + (c.nxl + 1) * ((j - B->yc[bq]) + (c.nyl + 1) * (k - B->zc[cq]));
                 by_sub[s].emplace_back(li, e.second);
@@ -773,4 +792,238 @@ extern "C" int sfm_project_receivers(sfm_handle* h, int nrec, const double* xyz)
     int rc = project_points(h, nrec, xyz, 1, 0.0, pp, ps, rows);
     if (rc) return rc;
     return sfm_set_receivers(h, nrec, (int)pp.size(), pp.data(), ps.data(), rows.data());
+}
+
+// ---------------------------------------------------------------------------
+// Surrogate mode of the offline stage
+// ---------------------------------------------------------------------------
+namespace {
+
+// velocity blocks of S subdomains of n^3 cells (origins in cells) as FP32
+__global__ void gather_blocks_kernel(const double* c, int gnx, int gny, const int3* origin, int S, int n,
+                                     float* out) {
+    const long long n3 = (long long)n * n * n, total = (long long)S * n3;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(t / n3);
+        const long long e = t - s * n3;
+        const int x = (int)(e % n), y = (int)((e / n) % n), z = (int)(e / ((long long)n * n));
+        const int3 o = origin[s];
+        out[t] = (float)c[((long long)(o.z + z) * gny + (o.y + y)) * gnx + (o.x + x)];
+    }
+}
+
+// Gamma_1 into level 0 (symmetrised) and Gammahat_1 into level k of each set
+__global__ void put_level1_kernel(const double* G1, const double* Gh1, int S, int b, int k, double* sets) {
+    const long long bb = (long long)b * b, total = (long long)S * bb;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(t / bb);
+        const int e = (int)(t - s * bb), r = e / b, c = e % b;
+        double* set = sets + (long long)s * 2 * k * bb;
+        set[e] = 0.5 * (G1[s * bb + r * b + c] + G1[s * bb + c * b + r]);
+        set[k * bb + e] = 0.5 * (Gh1[s * bb + r * b + c] + Gh1[s * bb + c * b + r]);
+    }
+}
+
+}  // namespace
+
+extern "C" int sfm_build_roms_surrogate(sfm_handle* h, sfm_net* net, const int* m_sub, const int* k_sub,
+                                        double sigma, double cg_tol, double nt_tol, const int* exact,
+                                        sfm_surrogate_report* srep, sfm_build_report* rep) {
+    if (!h) return SFM_ERR_ARG;
+    BuildState* B = bstate(h);
+    if (!B || !B->d_c) return bfail(h, SFM_ERR_STATE, "sfm_build_roms_surrogate: no model");
+    if (!net || !m_sub || !k_sub || !(sigma > 0.0) || !(nt_tol >= 0.0))
+        return bfail(h, SFM_ERR_ARG, "sfm_build_roms_surrogate: bad arguments");
+    int nn = 0, nb = 0, nk = 0;
+    if (sfm::net_shape(net, &nn, &nb, &nk) != SFM_OK)
+        return bfail(h, SFM_ERR_STATE, "sfm_build_roms_surrogate: the network has no decoder");
+    if (!(cg_tol > 0.0)) cg_tol = 1e-14;
+    BCK(h, cudaSetDevice(h->device));
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t st = h->stream;
+    cublasSetStream(B->blas, st);
+    cublasSetPointerMode(B->blas, CUBLAS_POINTER_MODE_HOST);
+    const Gemm gemm{B->blas};
+    const int ncx = (int)B->xc.size() - 1, ncy = (int)B->yc.size() - 1, ncz = (int)B->zc.size() - 1;
+    const int nsub = ncx * ncy * ncz;
+    // topology as the exact build forms it (coefficient layout for the presets)
+    std::vector<int> nbr(6 * nsub, -1), mface(6 * nsub, 0);
+    for (int s = 0; s < nsub; ++s) {
+        if (k_sub[s] < 1 || m_sub[s] < 1) return bfail(h, SFM_ERR_ARG, "sfm_build_roms_surrogate: m, k >= 1");
+        const int pos[3] = {s % ncx, (s / ncx) % ncy, s / (ncx * ncy)};
+        const int lim[3] = {ncx, ncy, ncz};
+        for (int f = 0; f < 6; ++f) {
+            int q[3] = {pos[0], pos[1], pos[2]};
+            q[f / 2] += (f & 1) ? 1 : -1;
+            if (q[f / 2] >= 0 && q[f / 2] < lim[f / 2]) nbr[s * 6 + f] = q[0] + ncx * (q[1] + ncy * q[2]);
+        }
+    }
+    for (int s = 0; s < nsub; ++s)
+        for (int f = 0; f < 6; ++f) {
+            const int t = nbr[s * 6 + f];
+            mface[s * 6 + f] = (t < 0) ? m_sub[s] : std::min(m_sub[s], m_sub[t]);
+        }
+    int rc = sfm::set_topology_internal(h, nsub, k_sub, mface.data(), nbr.data());
+    if (rc != SFM_OK) return rc;
+    // subdomains the network can serve: n^3 cells, k levels, the decoder's b
+    // with the same m on all six faces, and not marked exact by the caller
+    std::vector<int> elig;
+    std::vector<int3> org;
+    const int m = nb / 6;
+    for (int s = 0; s < nsub; ++s) {
+        const int ix = s % ncx, iy = (s / ncx) % ncy, iz = s / (ncx * ncy);
+        bool ok = (!exact || !exact[s]) && k_sub[s] == nk && nb % 6 == 0 &&
+                  B->xc[ix + 1] - B->xc[ix] == nn && B->yc[iy + 1] - B->yc[iy] == nn &&
+                  B->zc[iz + 1] - B->zc[iz] == nn;
+        for (int f = 0; f < 6 && ok; ++f) ok = mface[s * 6 + f] == m;
+        if (ok) {
+            elig.push_back(s);
+            org.push_back(make_int3(B->xc[ix], B->yc[iy], B->zc[iz]));
+        }
+    }
+    const int S = (int)elig.size();
+    std::vector<char> only(nsub, 1);
+    std::vector<double> herr(S, 0.0);
+    double* d_preset = nullptr;
+    DevGuard guard_preset(d_preset);
+    BCK(h, dmalloc(d_preset, (size_t)h->ncoef));
+    BCK(h, cudaMemsetAsync(d_preset, 0, (size_t)h->ncoef * sizeof(double), st));
+    int naccept = 0;
+    if (S > 0) {
+        const int b = nb, k = nk, N = (nn + 1) * (nn + 1) * (nn + 1);
+        const long long bb = (long long)b * b, sF = (long long)N * b;
+        int3* d_org = nullptr;
+        double *mass = nullptr, *Bm = nullptr, *F = nullptr, *LF = nullptr, *Gh1 = nullptr, *R0 = nullptr,
+               *R0i = nullptr, *Gi = nullptr, *A1 = nullptr, *T1 = nullptr, *G1 = nullptr, *Ss = nullptr,
+               *sets = nullptr, *d_err2 = nullptr, *serr = nullptr;
+        float *blocks = nullptr, *codes = nullptr;
+        ColSpec* d_cs = nullptr;
+        int* d_e = nullptr;
+        DevGuard g1(d_org);
+        DevGuard g2(mass, Bm, F, LF, Gh1, R0, R0i, Gi, A1, T1, G1, Ss, sets, d_err2, serr);
+        DevGuard g3(blocks, codes);
+        DevGuard g4(d_cs);
+        DevGuard g5(d_e);
+        BCK(h, dmalloc(d_org, S));
+        BCK(h, cudaMemcpyAsync(d_org, org.data(), S * sizeof(int3), cudaMemcpyHostToDevice, st));
+        BCK(h, dmalloc(mass, (size_t)S * N));
+        sfm::bld::mass_kernel<<<grid_for((long long)S * N), 256, 0, st>>>(B->d_c, B->gnx, B->gny, d_org, S,
+                                                                            nn, nn, nn, B->h, mass);
+        std::vector<ColSpec> cs;
+        for (int f = 0; f < 6; ++f)
+            for (auto pq : face_modes(nn - 1, nn - 1, m)) cs.push_back({f, pq.first, pq.second, 0});
+        BCK(h, dmalloc(d_cs, cs.size()));
+        BCK(h, cudaMemcpyAsync(d_cs, cs.data(), cs.size() * sizeof(ColSpec), cudaMemcpyHostToDevice, st));
+        BCK(h, dmalloc(Bm, (size_t)N * b));
+        sfm::bld::basis_kernel<<<grid_for((long long)N * b), 256, 0, st>>>(d_cs, b, nn, nn, nn, B->h, Bm);
+        // F = M^{-1/2} B
+        BCK(h, dmalloc(F, (size_t)S * sF));
+        sfm::bld::scale_kernel<<<grid_for((long long)S * sF), 256, 0, st>>>(Bm, 0, mass, F, sF, N, b, S, 1);
+        BCK(h, cudaGetLastError());
+        // level 1 closed forms: Gammahat_1 = F^T F, Gamma_1 = G^{-1} F^T L F G^{-1}
+        for (double** p : {&Gh1, &R0, &R0i, &Gi, &A1, &T1, &G1, &Ss}) BCK(h, dmalloc(*p, (size_t)S * bb));
+        BLK(h, gemm(true, false, b, b, N, 1.0, F, N, sF, F, N, sF, 0.0, Gh1, b, bb, S));
+        BCK(h, dmalloc(d_e, 1));
+        BCK(h, cudaMemsetAsync(d_e, 0, sizeof(int), st));
+        BCK(h, dmalloc(d_err2, (size_t)S));
+        const size_t csm = 2 * bb * sizeof(double);
+        BCK(h, cudaFuncSetAttribute(sfm::bld::chol_rinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)csm));
+        sfm::bld::chol_rinv_kernel<<<S, 128, csm, st>>>(Gh1, R0, R0i, b, d_e, d_err2);
+        BCK(h, cudaGetLastError());
+        BLK(h, gemm(false, true, b, b, b, 1.0, R0i, b, bb, R0i, b, bb, 0.0, Gi, b, bb, S));   // (F^T F)^{-1}
+        BCK(h, dmalloc(LF, (size_t)S * sF));
+        sfm::bld::op_kernel<<<S * b, 256, 0, st>>>(F, LF, mass, nn, nn, nn, B->h, 0.0, b, 1, nullptr);
+        BCK(h, cudaGetLastError());
+        BLK(h, gemm(true, false, b, b, N, 1.0, F, N, sF, LF, N, sF, 0.0, A1, b, bb, S));      // F^T L F
+        BLK(h, gemm(false, false, b, b, b, 1.0, Gi, b, bb, A1, b, bb, 0.0, T1, b, bb, S));
+        BLK(h, gemm(false, false, b, b, b, 1.0, T1, b, bb, Gi, b, bb, 0.0, G1, b, bb, S));
+        // one block solve: S(sigma) = F^T (L + sigma)^{-1} F, CG on (K + sigma M)
+        {
+            const size_t ncolv = (size_t)S * b;
+            double *Xc = nullptr, *Rc = nullptr, *Zc = nullptr, *Pc = nullptr, *Qc = nullptr, *rhs = nullptr,
+                   *rz = nullptr, *rz2 = nullptr, *pq = nullptr, *rr = nullptr, *rr0 = nullptr;
+            DevGuard guard_cg(Xc, Rc, Zc, Pc, Qc, rhs, rz, rz2, pq, rr, rr0);
+            for (double** p : {&Xc, &Rc, &Zc, &Pc, &Qc, &rhs}) BCK(h, dmalloc(*p, ncolv * N));
+            for (double** p : {&rz, &rz2, &pq, &rr, &rr0}) BCK(h, dmalloc(*p, ncolv));
+            sfm::bld::scale_kernel<<<grid_for((long long)ncolv * N), 256, 0, st>>>(F, sF, mass, rhs, sF, N, b, S, 0);
+            sfm::bld::cg_init_kernel<<<(int)ncolv, 256, 0, st>>>(rhs, Xc, Rc, Zc, Pc, mass, nn, nn, nn, B->h,
+                                                                 sigma, b, rz, rr0);
+            BCK(h, cudaGetLastError());
+            std::vector<double> h_rr(ncolv), h_rr0(ncolv);
+            BCK(h, cudaMemcpyAsync(h_rr0.data(), rr0, ncolv * sizeof(double), cudaMemcpyDeviceToHost, st));
+            int it = 0;
+            for (it = 1; it <= 20000; ++it) {
+                sfm::bld::op_kernel<<<(int)ncolv, 256, 0, st>>>(Pc, Qc, mass, nn, nn, nn, B->h, sigma, b, 0, pq);
+                sfm::bld::cg_update_kernel<<<(int)ncolv, 256, 0, st>>>(Xc, Rc, Zc, Pc, Qc, mass, nn, nn, nn, B->h,
+                                                                       sigma, b, rz, pq, rz2, rr);
+                sfm::bld::cg_dir_kernel<<<(int)ncolv, 256, 0, st>>>(Pc, Zc, N, rz, rz2);
+                if (it % 8 == 0) {
+                    BCK(h, cudaGetLastError());
+                    BCK(h, cudaMemcpyAsync(h_rr.data(), rr, ncolv * sizeof(double), cudaMemcpyDeviceToHost, st));
+                    BCK(h, cudaStreamSynchronize(st));
+                    double worst = 0.0;
+                    for (size_t i = 0; i < ncolv; ++i)
+                        if (h_rr0[i] > 0) worst = std::max(worst, std::sqrt(h_rr[i] / h_rr0[i]));
+                    if (worst < cg_tol) break;
+                }
+            }
+            if (it > 20000) return bfail(h, SFM_ERR_BREAKDOWN, "sfm_build_roms_surrogate: CG did not converge");
+            // W = M^{1/2} Y into LF, S(sigma) = F^T W
+            sfm::bld::scale_kernel<<<grid_for((long long)ncolv * N), 256, 0, st>>>(Xc, sF, mass, LF, sF, N, b, S, 0);
+            BCK(h, cudaGetLastError());
+            BLK(h, gemm(true, false, b, b, N, 1.0, F, N, sF, LF, N, sF, 0.0, Ss, b, bb, S));
+        }
+        // the network's coefficient sets: levels 2..k decoded, level 1 exact
+        BCK(h, dmalloc(blocks, (size_t)S * nn * nn * nn));
+        gather_blocks_kernel<<<grid_for((long long)S * nn * nn * nn), 256, 0, st>>>(B->d_c, B->gnx, B->gny, d_org,
+                                                                                    S, nn, blocks);
+        BCK(h, cudaGetLastError());
+        BCK(h, cudaStreamSynchronize(st));
+        BCK(h, dmalloc(sets, (size_t)S * 2 * k * bb));
+        BCK(h, cudaMemsetAsync(sets, 0, (size_t)S * 2 * k * bb * sizeof(double), st));
+        BCK(h, cudaStreamSynchronize(st));
+        const int ncode = sfm::net_code_dim(net);
+        BCK(h, dmalloc(codes, (size_t)S * ncode));
+        rc = sfm_net_forward(net, blocks, S, codes, 1);
+        if (rc != SFM_OK) return bfail(h, rc, std::string("sfm_build_roms_surrogate: network: ") + sfm_net_last_error(net));
+        rc = sfm_net_decode(net, codes, S, sets);
+        if (rc != SFM_OK) return bfail(h, rc, std::string("sfm_build_roms_surrogate: decoder: ") + sfm_net_last_error(net));
+        put_level1_kernel<<<grid_for((long long)S * bb), 256, 0, st>>>(G1, Gh1, S, b, k, sets);
+        BCK(h, cudaGetLastError());
+        // fallback test at sigma
+        BCK(h, dmalloc(serr, (size_t)S));
+        BCK(h, sfm::sigma_check(sets, S, b, k, sigma, Ss, serr, st));
+        BCK(h, cudaMemcpy(herr.data(), serr, S * sizeof(double), cudaMemcpyDeviceToHost));
+        for (int i = 0; i < S; ++i) {
+            const int s = elig[i];
+            if (herr[i] <= nt_tol) {
+                only[s] = 0;
+                ++naccept;
+                BCK(h, cudaMemcpyAsync(d_preset + h->coef_off[s], sets + (long long)i * 2 * k * bb,
+                                       2 * k * bb * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            }
+        }
+        BCK(h, cudaStreamSynchronize(st));
+    }
+    const double t_sur = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    const auto t1 = std::chrono::steady_clock::now();
+    rc = build_impl(h, m_sub, k_sub, sigma, cg_tol, rep, naccept > 0 ? &only : nullptr, d_preset);
+    if (rc != SFM_OK) return rc;
+    if (srep) {
+        srep->eligible = S;
+        srep->accepted = naccept;
+        srep->fallback = S - naccept;
+        std::vector<double> acc;
+        for (int i = 0; i < S; ++i)
+            if (herr[i] <= nt_tol) acc.push_back(herr[i]);
+        std::sort(herr.begin(), herr.end());
+        srep->sigma_err_median = S ? herr[S / 2] : 0.0;
+        srep->sigma_err_max_accepted = acc.empty() ? 0.0 : *std::max_element(acc.begin(), acc.end());
+        srep->seconds_surrogate = t_sur;
+        srep->seconds_exact = std::chrono::duration<double>(std::chrono::steady_clock::now() - t1).count();
+    }
+    return SFM_OK;
 }

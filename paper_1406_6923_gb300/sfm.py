@@ -41,7 +41,10 @@ EXPORTS = ["sfm_create", "sfm_destroy", "sfm_last_error", "sfm_set_stream", "sfm
            "sfm_run", "sfm_cfl_dt", "sfm_last_launches", "sfm_debug_set", "sfm_set_model",
            "sfm_build_roms", "sfm_project_sources", "sfm_project_receivers", "sfm_free_build", "sfm_run_static",
            "sfm_autotune", "sfm_set_initial", "sfm_plan_pieces", "sfm_usable_depths",
-           "sfm_cut_depth", "sfm_checkpoint", "sfm_restore", "sfm_run_report"]
+           "sfm_cut_depth", "sfm_checkpoint", "sfm_restore", "sfm_run_report",
+           "sfm_net_create", "sfm_net_destroy", "sfm_net_last_error", "sfm_net_params",
+           "sfm_net_grad", "sfm_net_adam", "sfm_net_forward", "sfm_raw_encode",
+           "sfm_net_fit_decoder", "sfm_net_decode", "sfm_ntd_error", "sfm_build_roms_surrogate"]
 
 
 class sfm_build_report(C.Structure):
@@ -56,6 +59,12 @@ class sfm_run_info(C.Structure):
                 ("status", C.c_int), ("unstable_step", C.c_int), ("energy", C.c_int)]
 
 
+class sfm_surrogate_report(C.Structure):
+    _fields_ = [("eligible", C.c_int), ("accepted", C.c_int), ("fallback", C.c_int),
+                ("sigma_err_median", C.c_double), ("sigma_err_max_accepted", C.c_double),
+                ("seconds_surrogate", C.c_double), ("seconds_exact", C.c_double)]
+
+
 class SfmError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"libsfm error {code}: {msg}")
@@ -68,6 +77,7 @@ _i = C.c_int
 _p = C.c_void_p
 _ip = C.POINTER(C.c_int)
 _dp = C.POINTER(C.c_double)
+_fp = C.POINTER(C.c_float)
 
 
 def load(path=LIB_PATH):
@@ -108,6 +118,19 @@ def load(path=LIB_PATH):
         "sfm_checkpoint": (_i, [_p, _p, C.POINTER(C.c_size_t)]),
         "sfm_restore": (_i, [_p, _p, C.c_size_t]),
         "sfm_run_report": (_i, [_p, C.POINTER(sfm_run_info), _dp, _i]),
+        "sfm_net_create": (_i, [C.POINTER(_p), _i, _i, _i, _i, _i, _i, _i, C.c_ulonglong]),
+        "sfm_net_destroy": (_i, [_p]),
+        "sfm_net_last_error": (C.c_char_p, [_p]),
+        "sfm_net_params": (_i, [_p, _fp, C.c_size_t, C.POINTER(C.c_size_t), _i]),
+        "sfm_net_grad": (_i, [_p, _p, _p, _i, _fp, _fp]),
+        "sfm_net_adam": (_i, [_p, C.c_float]),
+        "sfm_net_forward": (_i, [_p, _p, _i, _p, _i]),
+        "sfm_raw_encode": (_i, [_i, _i, _i, _i, _p, _p]),
+        "sfm_net_fit_decoder": (_i, [_p, _i, _i, _p, _i, _i, C.c_ulonglong, _p]),
+        "sfm_net_decode": (_i, [_p, _p, _i, _p]),
+        "sfm_ntd_error": (_i, [_i, _i, _i, _i, _p, _p, _i, _dp, _dp]),
+        "sfm_build_roms_surrogate": (_i, [_p, _p, _ip, _ip, C.c_double, C.c_double, C.c_double, _ip,
+                                          C.POINTER(sfm_surrogate_report), C.POINTER(sfm_build_report)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -363,3 +386,101 @@ def sfm_run_static(device, stream_ptr, k_sub, m_face, nbr, coeffs_ptr, nshots, s
                                _p(int(rec_rows_ptr)), float(dt), int(nsteps), _p(int(wavelet_ptr)),
                                _p(int(traces_ptr)))
     _check(None, rc)
+
+
+# ---------------------------------------------------------------------------
+# learned surrogate (network object)
+
+def _ncheck(net, rc):
+    if rc != SFM_OK:
+        msg = _lib.sfm_net_last_error(net) if net else _lib.sfm_last_error(None)
+        raise SfmError(rc, msg.decode() if msg else "")
+
+
+def sfm_net_create(device, n, c1, c2, c3, hidden, code, seed=0):
+    net = _p()
+    _ncheck(None, load().sfm_net_create(C.byref(net), int(device), int(n), int(c1), int(c2), int(c3),
+                                        int(hidden), int(code), int(seed)))
+    return net
+
+
+def sfm_net_destroy(net):
+    load().sfm_net_destroy(net)
+
+
+def sfm_net_params(net, values=None):
+    """Without ``values``: the parameters as an FP32 array; with: replace them."""
+    cnt = C.c_size_t(0)
+    _ncheck(net, load().sfm_net_params(net, None, 0, C.byref(cnt), 0))
+    if values is None:
+        out = np.empty(cnt.value, dtype=np.float32)
+        _ncheck(net, load().sfm_net_params(net, out.ctypes.data_as(_fp), out.size, C.byref(cnt), 0))
+        return out
+    v = np.ascontiguousarray(values, dtype=np.float32)
+    _ncheck(net, load().sfm_net_params(net, v.ctypes.data_as(_fp), v.size, C.byref(cnt), 1))
+    return None
+
+
+def sfm_net_grad(net, c_ptr, zt_ptr, batch, want_grad=False):
+    """Loss of a batch (device pointers) and, with ``want_grad``, the
+    gradient of every parameter as an FP32 array; returns (loss, grad)."""
+    loss = C.c_float(0.0)
+    g = None
+    if want_grad:
+        g = np.empty(sfm_net_params(net).size, dtype=np.float32)
+    _ncheck(net, load().sfm_net_grad(net, _p(int(c_ptr)), _p(int(zt_ptr)), int(batch), C.byref(loss),
+                                     g.ctypes.data_as(_fp) if g is not None else None))
+    return loss.value, g
+
+
+def sfm_net_adam(net, lr):
+    _ncheck(net, load().sfm_net_adam(net, float(lr)))
+
+
+def sfm_net_forward(net, c_ptr, batch, z_ptr, bf16=False):
+    _ncheck(net, load().sfm_net_forward(net, _p(int(c_ptr)), int(batch), _p(int(z_ptr)), 1 if bf16 else 0))
+
+
+def raw_size(b, k):
+    return 2 * (k - 1) * (b * (b - 1) // 2 + b)
+
+
+def sfm_raw_encode(device, count, b, k, coef_ptr, raw_ptr):
+    _ncheck(None, load().sfm_raw_encode(int(device), int(count), int(b), int(k), _p(int(coef_ptr)),
+                                        _p(int(raw_ptr))))
+
+
+def sfm_net_fit_decoder(net, b, k, raw_ptr, N, iters=4, seed=0, codes_ptr=None):
+    _ncheck(net, load().sfm_net_fit_decoder(net, int(b), int(k), _p(int(raw_ptr)), int(N), int(iters),
+                                            int(seed), _p(int(codes_ptr)) if codes_ptr else None))
+
+
+def sfm_net_decode(net, z_ptr, batch, coef_ptr):
+    _ncheck(net, load().sfm_net_decode(net, _p(int(z_ptr)), int(batch), _p(int(coef_ptr))))
+
+
+def sfm_ntd_error(device, count, b, k, coef_a_ptr, coef_r_ptr, lams):
+    """Relative NtD-map errors [count][len(lams)] of two coefficient families
+    (device pointers) at the complex ``lams``."""
+    lam = np.ascontiguousarray(np.stack([np.real(lams), np.imag(lams)], axis=1), dtype=np.float64)
+    err = np.empty((count, len(lams)))
+    _ncheck(None, load().sfm_ntd_error(int(device), int(count), int(b), int(k), _p(int(coef_a_ptr)),
+                                       _p(int(coef_r_ptr)), len(lams), lam.ctypes.data_as(_dp),
+                                       err.ctypes.data_as(_dp)))
+    return err
+
+
+def sfm_build_roms_surrogate(h, net, m_sub, k_sub, sigma, nt_tol, exact=None, cg_tol=1e-14):
+    """Offline stage with the surrogate and exact fallback; returns
+    (surrogate report dict, exact-build report dict)."""
+    m, mp = _iarr(m_sub)
+    k, kp = _iarr(k_sub)
+    ep = None
+    if exact is not None:
+        e, ep = _iarr(np.asarray(exact, dtype=np.int32))
+    srep = sfm_surrogate_report()
+    rep = sfm_build_report()
+    _check(h, load().sfm_build_roms_surrogate(h, net, mp, kp, float(sigma), float(cg_tol), float(nt_tol),
+                                              ep, C.byref(srep), C.byref(rep)))
+    return ({n: getattr(srep, n) for n, _ in sfm_surrogate_report._fields_},
+            {n: getattr(rep, n) for n, _ in sfm_build_report._fields_})
