@@ -232,7 +232,9 @@ int sfm_cfl_dt(sfm_handle* h, int iters, double* lambda_max, double* dt_cfl);
  * counterpart in the paper, whose method fixes no launch shape).  Each
  * candidate block shape - consumer warps in {2,4,6,8} times
  * coefficient ring stages in {2,3,4,6,8,12,16}, those whose shared memory
- * fits (for SFM_FP32F only stage counts that are multiples of the warps) -
+ * fits (for SFM_FP32F only stage counts that are multiples of the warps,
+ * each with the single- and the paired-product kernel; for the panel modes
+ * 16-shot groups per task in {1, 2, 4, 8} times stages in {2, 3, 4, 6, 8}) -
  * steps the coupled system `nsteps` steps from rest with a zero source
  * twice (a state from sfm_set_initial or sfm_restore is left aside for
  * the probes and kept for the next sfm_run); the
@@ -485,8 +487,11 @@ int sfm_net_forward(sfm_net* net, const float* c, int B, float* z, int bf16);
  *   of N raw targets [N][nraw] (device) and P [nraw][code], an orthonormal
  *   basis of their leading principal subspace by randomized subspace
  *   iteration (Halko, Martinsson and Tropp) with `iters` power passes and
- *   Cholesky-QR orthonormalisation; codes (device FP32 [N][code], may be
- *   NULL) receive the targets' codes P^T (raw - mu).  N >= code.
+ *   Cholesky-QR orthonormalisation, each column then scaled by the RMS of
+ *   its coordinate over the targets (so codes are of order one and
+ *   mu + P z is unchanged); codes (device FP32 [N][code], may be NULL)
+ *   receive the targets' codes (least-squares coordinates in that basis).
+ *   N >= code.
  * sfm_net_decode: coefficient sets (device FP64, B sets) of B codes (device
  *   FP32): levels 2..k written from mu + P z, level 1 left untouched.
  * sfm_ntd_error: err[i][l] = |S_a - S_r|_F / |S_r|_F of two families of
@@ -516,9 +521,11 @@ int sfm_ntd_error(int device, int count, int b, int k, const double* coef_a, con
  * subdomains, in batches on the device: level 1 from its closed forms
  * (Gammahat_1 = F^T F, Gamma_1 = Gammahat_1^{-1} F^T L F Gammahat_1^{-1}),
  * levels 2..k from the network (BF16 inference) and its decoder, and one
- * block solve S(sigma) = F^T (L + sigma)^{-1} F (CG to cg_tol); a subdomain
- * whose decoded S-fraction misses S(sigma) by more than nt_tol (relative
- * Frobenius) falls back to the exact build, which then runs for the
+ * block solve W = (L + sigma)^{-1} F (CG to cg_tol), which gives the exact
+ * S(sigma) = F^T W and S'(sigma) = -W^T W; a subdomain whose decoded
+ * S-fraction misses either by more than nt_tol (relative Frobenius; its
+ * derivative by a central difference) falls back to the exact build, which
+ * then runs for the
  * fallbacks and every subdomain not served (as sfm_build_roms would, with
  * the same m_sub, k_sub, sigma and cg_tol).  Coefficients of served
  * subdomains carry no Krylov basis: sources and receivers must not touch
@@ -531,7 +538,8 @@ typedef struct sfm_surrogate_report {
     int eligible;                 /* subdomains the network served             */
     int accepted;                 /* ... whose S(sigma) passed nt_tol          */
     int fallback;                 /* ... rebuilt exactly                       */
-    double sigma_err_median;      /* median relative S(sigma) error, served    */
+    double sigma_err_median;      /* median of the larger relative error of
+                                     S(sigma) and S'(sigma), served            */
     double sigma_err_max_accepted;
     double seconds_surrogate;     /* wall time of the surrogate pass           */
     double seconds_exact;         /* wall time of the exact build that followed */
@@ -566,7 +574,11 @@ int sfm_last_launches(const sfm_handle* h, int* launches);
  *   key 3: consumer warps per stepping block (1..8), all precisions;
  *   key 4: coefficient ring stages per stepping block (2..16), all
  *          precisions (keys 3 and 4 override sfm_autotune's choice; for
- *          SFM_FP32F the stages are rounded up to a multiple of the warps).
+ *          SFM_FP32F the stages are rounded up to a multiple of the warps);
+ *   key 5: SFM_FP32F kernel: 0 = one factor product per warp at a time,
+ *          1 = a warp's two owned blocks applied together (interleaved
+ *          products; used on 48-wide blocks when the ring holds two stages
+ *          per warp).  Both give bitwise the same traces.
  * Errors: SFM_ERR_ARG for an unknown key or a value out of range.
  */
 int sfm_debug_set(sfm_handle* h, int key, long long value);

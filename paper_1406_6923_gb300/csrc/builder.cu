@@ -975,6 +975,8 @@ extern "C" int sfm_build_roms_surrogate(sfm_handle* h, sfm_net* net, const int* 
             sfm::bld::scale_kernel<<<grid_for((long long)ncolv * N), 256, 0, st>>>(Xc, sF, mass, LF, sF, N, b, S, 0);
             BCK(h, cudaGetLastError());
             BLK(h, gemm(true, false, b, b, N, 1.0, F, N, sF, LF, N, sF, 0.0, Ss, b, bb, S));
+            // S'(sigma) = -F^T (L + sigma)^{-2} F = -W^T W from the same solve
+            BLK(h, gemm(true, false, b, b, N, -1.0, LF, N, sF, LF, N, sF, 0.0, A1, b, bb, S));
         }
         // the network's coefficient sets: levels 2..k decoded, level 1 exact
         BCK(h, dmalloc(blocks, (size_t)S * nn * nn * nn));
@@ -995,7 +997,7 @@ extern "C" int sfm_build_roms_surrogate(sfm_handle* h, sfm_net* net, const int* 
         BCK(h, cudaGetLastError());
         // fallback test at sigma
         BCK(h, dmalloc(serr, (size_t)S));
-        BCK(h, sfm::sigma_check(sets, S, b, k, sigma, Ss, serr, st));
+        BCK(h, sfm::sigma_check(sets, S, b, k, sigma, Ss, A1, serr, st));
         BCK(h, cudaMemcpy(herr.data(), serr, S * sizeof(double), cudaMemcpyDeviceToHost));
         for (int i = 0; i < S; ++i) {
             const int s = elig[i];

@@ -219,6 +219,36 @@ __device__ __forceinline__ void readout_level(const PanelParams& p, int b, int j
     }
 }
 
+// The same from rows staged in shared memory: rows[e * rstride + i] is row
+// i of pair e's block at this level.
+template <int NT>
+__device__ __forceinline__ void readout_level_s(const float* rows, int rstride, int b, int nrp,
+                                                const float (&u)[NT][4], float* acc) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    for (int e = 0; e < nrp; ++e) {
+        const float* row = rows + e * rstride;
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+            const int r0 = 8 * nt + 2 * t;
+            const float a = r0 < b ? row[r0] : 0.f;
+            const float c = r0 + 1 < b ? row[r0 + 1] : 0.f;
+            s0 = fmaf(a, u[nt][0], s0);
+            s1 = fmaf(a, u[nt][2], s1);
+            s0 = fmaf(c, u[nt][1], s0);
+            s1 = fmaf(c, u[nt][3], s1);
+        }
+        s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+        s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+        if (t == 0) {
+            acc[e * 16 + 2 * g] += s0;
+            acc[e * 16 + 2 * g + 1] += s1;
+        }
+    }
+}
+
 // The unit's readout sums of sample n to the partial buffer, then cleared.
 __device__ __forceinline__ void flush_readout(const PanelParams& p, int g, int n, int rp0, int nrp,
                                               float* acc) {
@@ -244,9 +274,15 @@ struct Ring {
 };
 
 __device__ __forceinline__ const float* ring_take(Ring& r, const float* stages, int stage_elems,
-                                                  unsigned long long* full, const PanelParams& p) {
-    if (!r.dead && !mbar_wait(full + r.st, r.ph, p.err, p.timeout_ns)) r.dead = true;
+                                                  unsigned long long* full, int* err,
+                                                  unsigned long long timeout_ns) {
+    if (!r.dead && !mbar_wait(full + r.st, r.ph, err, timeout_ns)) r.dead = true;
     return r.dead ? nullptr : stages + (size_t)r.st * stage_elems;
+}
+
+__device__ __forceinline__ const float* ring_take(Ring& r, const float* stages, int stage_elems,
+                                                  unsigned long long* full, const PanelParams& p) {
+    return ring_take(r, stages, stage_elems, full, p.err, p.timeout_ns);
 }
 
 __device__ __forceinline__ void ring_give(Ring& r, unsigned long long* empty, int nstage) {
@@ -255,15 +291,59 @@ __device__ __forceinline__ void ring_give(Ring& r, unsigned long long* empty, in
     if (++r.st == nstage) { r.st = 0; r.ph ^= 1u; }
 }
 
+// Shared-memory panel slots of a warp: one level's b x 16 panel with a row
+// stride of PROW floats (16 numbers + 4 of padding: rows 2t of the
+// accumulator pattern then fall on distinct bank pairs for every t, so the
+// float2 reads below are conflict free).
+constexpr int PROW = 20;
+constexpr int NSLOT = 5;           // U ring of 3, delta ring of 2
+constexpr int RHO_STAGE_MAX = 8;   // receiver pairs per subdomain staged with the state
+
+// Floats of a warp's shared-memory region: the state slots, two levels of
+// staged receiver rows (when rpmax <= RHO_STAGE_MAX) and their offsets,
+// rounded up to 128 bytes so that every warp's region (and the 16-byte
+// copies into its slots) starts aligned.
+__host__ __device__ inline long long warp_region_floats(int bmax, int rpmax) {
+    const long long bpad = ((bmax + 7) / 8) * 8;
+    const long long rho = rpmax <= RHO_STAGE_MAX ? rpmax : 0;
+    const long long n = NSLOT * bpad * PROW + 2 * rho * bpad + 2 * rho;
+    return (n + 31) / 32 * 32;
+}
+
+// Asynchronous copy (16-byte cp.async) of one level's panel (b rows of 16
+// numbers, contiguous in global memory) into a slot.
+__device__ __forceinline__ void stage_panel(float* slot, const float* src, int b) {
+    const int lane = threadIdx.x & 31;
+    for (int i = lane; i < b * 4; i += 32) {
+        const int r = i >> 2, c = i & 3;
+        cp_async<16>(slot + r * PROW + 4 * c, src + r * 16 + 4 * c);
+    }
+}
+
+template <int NT>
+__device__ __forceinline__ void lds_panel(const float* slot, int b, float (&v)[NT][4]) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+        const int r0 = 8 * nt + 2 * t;
+        float2 a = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+        if (r0 < b) a = *reinterpret_cast<const float2*>(slot + r0 * PROW + 2 * g);
+        if (r0 + 1 < b) c = *reinterpret_cast<const float2*>(slot + (r0 + 1) * PROW + 2 * g);
+        v[nt][0] = a.x; v[nt][2] = a.y; v[nt][1] = c.x; v[nt][3] = c.y;
+    }
+}
+
 // Phase A of unit (group g, subdomain s) at step n (see the file comment).
-// Only phi_{j-1} is carried from level to level; U_j, U_{j+1}, delta_j and
-// the source rows are loaded where they are used (U_{j+1} read at level j is
-// read again at level j+1 from the L1 cache), which keeps the live registers
-// of a level to phi_{j-1}, the split fragments and two product panels.
+// The warp stages the state it reads into its own slots one level ahead:
+// copy group 0 holds U_0 and U_1, group j >= 1 holds U_{j+1} and delta_j,
+// and group j+2 is issued as soon as level j has finished with the slots of
+// U_j and delta_j, so the copies of the next levels run while this level's
+// products do.  Only phi_{j-1} is carried from level to level in registers.
 template <int NT, int MODE>
 __device__ __noinline__ void unit_a(const PanelParams& p, int s, int g, int b, int k, int n, float* mail,
-                       float* acc, Ring& ring, const float* stages, int stage_elems,
+                       float* acc, float* slots, Ring& ring_io, const float* stages, int stage_elems,
                        unsigned long long* full, unsigned long long* empty) {
+    Ring ring = ring_io;               // in registers for the level loop
     const int lane = threadIdx.x & 31, gg = lane >> 2;
     const long long so = ((long long)g * p.nstate + p.state_off[s]) * 16;
     float* U = p.U + so;
@@ -275,14 +355,59 @@ __device__ __noinline__ void unit_a(const PanelParams& p, int s, int g, int b, i
     const int rp0 = p.sub_rp_ptr[s], nrp = p.sub_rp_ptr[s + 1] - rp0;
     const float dt2 = p.dt2;
     const long long lb = (long long)b * 16;
+    // fields the level loop needs, read once (the parameter block is not
+    // in registers inside this function)
+    int* const err = p.err;
+    const unsigned long long tmo = p.timeout_ns;
+    const int nstage = p.nstage;
+    const int bpad = ((p.bmax + 7) / 8) * 8;
+    const int ss = bpad * PROW;                            // floats per slot
+    float* Us = slots;                                     // U slots 0..2
+    float* Ds = slots + 3 * ss;                            // delta slots 0..1
+    // receiver rows of levels j (parity j & 1), with the pairs' row offsets
+    const bool rho_st = p.rpmax <= RHO_STAGE_MAX && nrp > 0;
+    float* Rs = slots + NSLOT * ss;
+    const int rsz = p.rpmax * bpad;
+    long long* rpb = reinterpret_cast<long long*>(Rs + 2 * rsz);
+    const float* rrows = p.rrows;
+    if (rho_st) {
+        for (int e = lane; e < nrp; e += 32) rpb[e] = p.rp_off[p.sub_rp[rp0 + e]];
+        __syncwarp();
+    }
+    // group j of copies (see above; with receivers also their rows of
+    // level j); an empty group is committed too, so the group count stays
+    // the same in every lane
+    auto issue = [&](int j) {
+        if (j == 0) {
+            stage_panel(Us, U, b);
+            if (k > 1) stage_panel(Us + ss, U + lb, b);
+        } else if (j < k) {
+            if (j + 1 < k) stage_panel(Us + ((j + 1) % 3) * ss, U + (j + 1) * lb, b);
+            stage_panel(Ds + (j & 1) * ss, D + j * lb, b);
+        }
+        if (rho_st && j < k)
+            for (int e = 0; e < nrp; ++e)
+                for (int i = lane; i < b; i += 32)
+                    cp_async<4>(Rs + (j & 1) * rsz + e * bpad + i, rrows + rpb[e] + (long long)j * b + i);
+        cp_async_commit();
+    };
+    __syncwarp();
+    issue(0);
+    issue(1);
     float phiprev[NT][4];
     for (int j = 0; j < k; ++j) {
+        cp_async_wait<1>();
+        __syncwarp();
+        const float* Uj = Us + (j % 3) * ss;
+        const float* Uj1 = Us + ((j + 1) % 3) * ss;
+        const float* Dj = Ds + (j & 1) * ss;
         float x[NT][4], y[NT][4];
         // Delta_j = U_{j+1} - U_j (U_k = 0), and the readout of U_j^n
-        ld_panel<NT>(U + j * lb, b, y);
-        if (nrp > 0) readout_level<NT>(p, b, j, rp0, nrp, y, acc);
+        lds_panel<NT>(Uj, b, y);
+        if (rho_st) readout_level_s<NT>(Rs + (j & 1) * rsz, bpad, b, nrp, y, acc);
+        else if (nrp > 0) readout_level<NT>(p, b, j, rp0, nrp, y, acc);
         if (j + 1 < k) {
-            ld_panel<NT>(U + (j + 1) * lb, b, x);
+            lds_panel<NT>(Uj1, b, x);
         } else {
 #pragma unroll
             for (int i = 0; i < NT; ++i)
@@ -293,9 +418,9 @@ __device__ __noinline__ void unit_a(const PanelParams& p, int s, int g, int b, i
         for (int i = 0; i < NT; ++i)
 #pragma unroll
             for (int e = 0; e < 4; ++e) x[i][e] -= y[i][e];
-        const float* tl = ring_take(ring, stages, stage_elems, full, p);
+        const float* tl = ring_take(ring, stages, stage_elems, full, err, tmo);
         if (tl) factor_panel<NT, MODE>(tl, x, y);     // y = phi_j
-        ring_give(ring, empty, p.nstage);
+        ring_give(ring, empty, nstage);
         // x = p_j f(t_n)
         if (src) {
             ld_panel<NT>(src + j * lb, b, x);
@@ -328,18 +453,18 @@ __device__ __noinline__ void unit_a(const PanelParams& p, int s, int g, int b, i
                     x[i][e] = (y[i][e] - phiprev[i][e]) + x[i][e];
                     phiprev[i][e] = y[i][e];
                 }
-            tl = ring_take(ring, stages, stage_elems, full, p);
+            tl = ring_take(ring, stages, stage_elems, full, err, tmo);
             if (tl) factor_panel<NT, MODE>(tl, x, y);     // y = a_j
-            ring_give(ring, empty, p.nstage);
+            ring_give(ring, empty, nstage);
             if (tl) {
                 // (2.2) increment and state update, Eq. (19)
-                ld_panel<NT>(D + j * lb, b, x);
+                lds_panel<NT>(Dj, b, x);
 #pragma unroll
                 for (int i = 0; i < NT; ++i)
 #pragma unroll
                     for (int e = 0; e < 4; ++e) x[i][e] = fmaf(dt2, y[i][e], x[i][e]);
                 st_panel<NT>(D + j * lb, b, x);
-                ld_panel<NT>(U + j * lb, b, y);
+                lds_panel<NT>(Uj, b, y);
 #pragma unroll
                 for (int i = 0; i < NT; ++i)
 #pragma unroll
@@ -347,7 +472,13 @@ __device__ __noinline__ void unit_a(const PanelParams& p, int s, int g, int b, i
                 st_panel<NT>(U + j * lb, b, y);
             }
         }
+        // the slots of U_j and delta_j are free: stage two levels ahead
+        __syncwarp();
+        issue(j + 2);
     }
+    cp_async_wait<0>();
+    __syncwarp();
+    ring_io = ring;
     if (nrp > 0) flush_readout(p, g, n, rp0, nrp, acc);
 }
 
@@ -406,18 +537,18 @@ __device__ void unit_b(const PanelParams& p, int s, int g, int b, int n, const f
 
 template <int MODE>
 __device__ __forceinline__ void unit_a_any(int nt, const PanelParams& p, int s, int g, int b, int k,
-                                           int n, float* mail, float* acc, Ring& ring,
+                                           int n, float* mail, float* acc, float* slots, Ring& ring,
                                            const float* stages, int stage_elems,
                                            unsigned long long* full, unsigned long long* empty) {
     switch (nt) {
-        case 1: unit_a<1, MODE>(p, s, g, b, k, n, mail, acc, ring, stages, stage_elems, full, empty); break;
-        case 2: unit_a<2, MODE>(p, s, g, b, k, n, mail, acc, ring, stages, stage_elems, full, empty); break;
-        case 3: unit_a<3, MODE>(p, s, g, b, k, n, mail, acc, ring, stages, stage_elems, full, empty); break;
-        case 4: unit_a<4, MODE>(p, s, g, b, k, n, mail, acc, ring, stages, stage_elems, full, empty); break;
-        case 5: unit_a<5, MODE>(p, s, g, b, k, n, mail, acc, ring, stages, stage_elems, full, empty); break;
-        case 6: unit_a<6, MODE>(p, s, g, b, k, n, mail, acc, ring, stages, stage_elems, full, empty); break;
-        case 7: unit_a<7, MODE>(p, s, g, b, k, n, mail, acc, ring, stages, stage_elems, full, empty); break;
-        default: unit_a<8, MODE>(p, s, g, b, k, n, mail, acc, ring, stages, stage_elems, full, empty); break;
+        case 1: unit_a<1, MODE>(p, s, g, b, k, n, mail, acc, slots, ring, stages, stage_elems, full, empty); break;
+        case 2: unit_a<2, MODE>(p, s, g, b, k, n, mail, acc, slots, ring, stages, stage_elems, full, empty); break;
+        case 3: unit_a<3, MODE>(p, s, g, b, k, n, mail, acc, slots, ring, stages, stage_elems, full, empty); break;
+        case 4: unit_a<4, MODE>(p, s, g, b, k, n, mail, acc, slots, ring, stages, stage_elems, full, empty); break;
+        case 5: unit_a<5, MODE>(p, s, g, b, k, n, mail, acc, slots, ring, stages, stage_elems, full, empty); break;
+        case 6: unit_a<6, MODE>(p, s, g, b, k, n, mail, acc, slots, ring, stages, stage_elems, full, empty); break;
+        case 7: unit_a<7, MODE>(p, s, g, b, k, n, mail, acc, slots, ring, stages, stage_elems, full, empty); break;
+        default: unit_a<8, MODE>(p, s, g, b, k, n, mail, acc, slots, ring, stages, stage_elems, full, empty); break;
     }
 }
 
@@ -442,14 +573,15 @@ __device__ __forceinline__ void final_readout_any(int nt, const PanelParams& p, 
 // shared-memory stages; all consumer warps read every stage (a task's warps
 // work on the same subdomain), warps without a group pass over it.
 template <int MODE>
-__global__ void __launch_bounds__(PANEL_BLOCK_MAX) panel_kernel(PanelParams p) {
+__global__ void __launch_bounds__(PANEL_BLOCK_MAX) panel_kernel(const __grid_constant__ PanelParams p) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int ncw = p.ncw, nct = ncw * 32, nstage = p.nstage;
     const int stage_elems = (int)(tri_tiles(p.bmax) * PTILE);
     const int bpad = ((p.bmax + 7) / 8) * 8;
     float* stages = reinterpret_cast<float*>(smem_raw);
-    float* scr_all = stages + (size_t)nstage * stage_elems;          // ncw x bpad*16
-    float* acc_all = scr_all + (size_t)ncw * bpad * 16;             // ncw x rpmax*16
+    const long long wreg = warp_region_floats(p.bmax, p.rpmax);
+    float* slot_all = stages + (size_t)nstage * stage_elems;         // ncw x wreg
+    float* acc_all = slot_all + (size_t)ncw * wreg;                 // ncw x rpmax*16
     unsigned long long* full = reinterpret_cast<unsigned long long*>(
         (reinterpret_cast<uintptr_t>(acc_all + (size_t)ncw * p.rpmax * 16) + 15) & ~(uintptr_t)15);
     unsigned long long* empty = full + nstage;
@@ -500,7 +632,8 @@ __global__ void __launch_bounds__(PANEL_BLOCK_MAX) panel_kernel(PanelParams p) {
     }
 
     // ------------------------------- consumers --------------------------------
-    float* scr = scr_all + (size_t)warp * bpad * 16;
+    float* slots = slot_all + (size_t)warp * wreg;
+    float* scr = slots;                  // phase B's face sums reuse the first slot
     float* acc = acc_all + (size_t)warp * p.rpmax * 16;
     Ring ring{0, 0u, false};
     for (int n = 0; n < p.nsteps; ++n) {
@@ -509,7 +642,7 @@ __global__ void __launch_bounds__(PANEL_BLOCK_MAX) panel_kernel(PanelParams p) {
             const int4 T = p.task[tk];
             const int s = T.x, b = T.w & 255, k = T.w >> 8;
             if (warp < T.z) {
-                unit_a_any<MODE>((b + 7) >> 3, p, s, T.y + warp, b, k, n, mail, acc, ring, stages,
+                unit_a_any<MODE>((b + 7) >> 3, p, s, T.y + warp, b, k, n, mail, acc, slots, ring, stages,
                                  stage_elems, full, empty);
             } else {
                 for (int m = 0; m < 2 * k - 1; ++m) {
@@ -534,8 +667,9 @@ __global__ void __launch_bounds__(PANEL_BLOCK_MAX) panel_kernel(PanelParams p) {
 
 size_t panel_smem_bytes(int ncw, int nstage, int bmax, int rpmax) {
     const size_t bpad = (size_t)((bmax + 7) / 8) * 8;
-    size_t bytes = sizeof(float) * ((size_t)nstage * tri_tiles(bmax) * PTILE + (size_t)ncw * bpad * 16 +
-                                    (size_t)ncw * rpmax * 16);
+    (void)bpad;
+    size_t bytes = sizeof(float) * ((size_t)nstage * tri_tiles(bmax) * PTILE +
+                                    (size_t)ncw * warp_region_floats(bmax, rpmax) + (size_t)ncw * rpmax * 16);
     bytes = (bytes + 15) & ~(size_t)15;
     return bytes + 2 * (size_t)nstage * sizeof(unsigned long long);
 }

@@ -137,12 +137,12 @@ cudaError_t launch_state_to_f64(const T* in, double* out, size_t n, cudaStream_t
 
 // surrogate helpers (surrogate.cu): the network's block side and the (b, k)
 // of its decoder (SFM_ERR_STATE without a decoder); the relative error of
-// the transfer functions at sigma of `count` coefficient sets against real
-// b x b references
+// the transfer functions at sigma of `count` coefficient sets, and of their
+// derivatives there, against real b x b references (Dref may be NULL)
 int net_shape(const sfm_net* net, int* n, int* b, int* k);
 int net_code_dim(const sfm_net* net);
 cudaError_t sigma_check(const double* sets, int count, int b, int k, double sigma, const double* Sref,
-                        double* err, cudaStream_t st);
+                        const double* Dref, double* err, cudaStream_t st);
 
 // launchers (step.cu); P is a number policy of numeric.cuh
 template <class P>

@@ -782,6 +782,29 @@ __global__ void rsolve_kernel(double* Q, long long rows, int d, const double* R)
     }
 }
 
+// per-column RMS of the (centred) codes C [N][d]; zero columns give 1
+__global__ void code_rms_kernel(const double* C, int N, int d, double* sd) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= d) return;
+    double s = 0.0;
+    for (int r = 0; r < N; ++r) s += C[(long long)r * d + c] * C[(long long)r * d + c];
+    s = sqrt(s / N);
+    sd[c] = s > 0.0 ? s : 1.0;
+}
+
+// P[r][c] *= sd[c] (rows = nraw) and C[r][c] /= sd[c] (rows = N)
+__global__ void rescale_kernel(double* P, long long nraw, double* C, int N, int d, const double* sd) {
+    const long long total = nraw * d + (long long)N * d;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (i < nraw * d) P[i] *= sd[i % d];
+        else {
+            const long long j = i - nraw * d;
+            C[j] /= sd[j % d];
+        }
+    }
+}
+
 __global__ void f64_to_f32_kernel(const double* in, float* out, long long n) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
@@ -1047,12 +1070,18 @@ extern "C" int sfm_net_fit_decoder(sfm_net* net, int b, int k, const double* raw
         cleanup();
         return nfail(net, SFM_ERR_BREAKDOWN, "sfm_net_fit_decoder: rank-deficient targets");
     }
+    // codes of the targets, then each code coordinate scaled to unit RMS
+    // over the targets (P's column scaled back, so mu + P z is unchanged):
+    // the network then learns numbers of order one
+    FCK((dgemm<false, false>(st, N, d, (int)nraw, 1.0, Rc, (int)nraw, net->P, d, 0.0, C64, d)));
+    code_rms_kernel<<<(d + 127) / 128, 128, 0, st>>>(C64, N, d, G);
+    rescale_kernel<<<grid1(nraw * d + (long long)N * d), 256, 0, st>>>(net->P, nraw, C64, N, d, G);
+    FCK(cudaGetLastError());
     if (codes) {
-        FCK((dgemm<false, false>(st, N, d, (int)nraw, 1.0, Rc, (int)nraw, net->P, d, 0.0, C64, d)));
         f64_to_f32_kernel<<<grid1((long long)N * d), 256, 0, st>>>(C64, codes, (long long)N * d);
         FCK(cudaGetLastError());
-        FCK(cudaStreamSynchronize(st));
     }
+    FCK(cudaStreamSynchronize(st));
 #undef FCK
     cleanup();
     return SFM_OK;
@@ -1123,24 +1152,48 @@ namespace sur {
 // err[i] = |S_i(sigma) - Sref_i|_F / |Sref_i|_F, S_i the transfer function of
 // coefficient set i (complex evaluation at lambda = sigma, imaginary part 0)
 // and Sref_i a real b x b matrix
-__global__ void sigma_err_kernel(const double* S, const double* Sref, int bb, double* err) {
-    __shared__ double na[256], nr[256];
+// err[i] = max(|S_i(sigma) - Sref_i| / |Sref_i|, |S_i'(sigma) - Dref_i| / |Dref_i|)
+// (Frobenius norms): S_i the transfer function of coefficient set i, its
+// derivative by the central difference of the values at sigma (1 -+ eps)
+// (S holds nl = 1 or 3 lambdas per set, complex with zero imaginary part),
+// Sref, Dref real b x b (Dref NULL: the value alone)
+__global__ void sigma_err_kernel(const double* S, const double* Sref, int bb, int nl, const double* Dref,
+                                 double dl, double* err) {
+    __shared__ double na[256], nr[256], ma[256], mr[256];
     const int i = blockIdx.x;
-    double a = 0.0, r = 0.0;
+    const double* s0 = S + (long long)i * nl * 2 * bb;
+    double a = 0.0, r = 0.0, c = 0.0, q = 0.0;
     for (int e = threadIdx.x; e < bb; e += blockDim.x) {
-        const double re = S[(long long)i * 2 * bb + 2 * e], im = S[(long long)i * 2 * bb + 2 * e + 1];
+        const double re = s0[2 * e], im = s0[2 * e + 1];
         const double f = Sref[(long long)i * bb + e];
         a += (re - f) * (re - f) + im * im;
         r += f * f;
+        if (Dref) {
+            const double dv = (s0[4 * bb + 2 * e] - s0[2 * bb + 2 * e]) / dl;
+            const double g = Dref[(long long)i * bb + e];
+            c += (dv - g) * (dv - g);
+            q += g * g;
+        }
     }
     na[threadIdx.x] = a;
     nr[threadIdx.x] = r;
+    ma[threadIdx.x] = c;
+    mr[threadIdx.x] = q;
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) { na[threadIdx.x] += na[threadIdx.x + s]; nr[threadIdx.x] += nr[threadIdx.x + s]; }
+        if ((int)threadIdx.x < s) {
+            na[threadIdx.x] += na[threadIdx.x + s];
+            nr[threadIdx.x] += nr[threadIdx.x + s];
+            ma[threadIdx.x] += ma[threadIdx.x + s];
+            mr[threadIdx.x] += mr[threadIdx.x + s];
+        }
         __syncthreads();
     }
-    if (threadIdx.x == 0) err[i] = sqrt(na[0] / nr[0]);
+    if (threadIdx.x == 0) {
+        double v = sqrt(na[0] / nr[0]);
+        if (Dref) v = fmax(v, sqrt(ma[0] / mr[0]));
+        err[i] = v;
+    }
 }
 
 }  // namespace sur
@@ -1156,15 +1209,18 @@ int net_shape(const sfm_net* net, int* n, int* b, int* k) {
 int net_code_dim(const sfm_net* net) { return net ? net->code : 0; }
 
 cudaError_t sigma_check(const double* sets, int count, int b, int k, double sigma, const double* Sref,
-                        double* err, cudaStream_t st) {
+                        const double* Dref, double* err, cudaStream_t st) {
+    // lambda = sigma, and sigma (1 -+ eps) for the central difference of S
+    const double eps = 1e-4;
+    const int nl = Dref ? 3 : 1;
     double *lam = nullptr, *S = nullptr;
-    cudaError_t e = nalloc(lam, 2);
-    if (e == cudaSuccess) e = nalloc(S, (size_t)count * 2 * b * b);
-    const double hl[2] = {sigma, 0.0};
+    cudaError_t e = nalloc(lam, 6);
+    if (e == cudaSuccess) e = nalloc(S, (size_t)count * nl * 2 * b * b);
+    const double hl[6] = {sigma, 0.0, sigma * (1.0 - eps), 0.0, sigma * (1.0 + eps), 0.0};
     if (e == cudaSuccess) e = cudaMemcpyAsync(lam, hl, sizeof(hl), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = sur::launch_transfer(sets, count, b, k, lam, 1, S, st);
+    if (e == cudaSuccess) e = sur::launch_transfer(sets, count, b, k, lam, nl, S, st);
     if (e == cudaSuccess) {
-        sur::sigma_err_kernel<<<count, 256, 0, st>>>(S, Sref, b * b, err);
+        sur::sigma_err_kernel<<<count, 256, 0, st>>>(S, Sref, b * b, nl, Dref, 2.0 * sigma * eps, err);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
