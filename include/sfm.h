@@ -232,8 +232,8 @@ int sfm_cfl_dt(sfm_handle* h, int iters, double* lambda_max, double* dt_cfl);
  * counterpart in the paper, whose method fixes no launch shape).  Each
  * candidate block shape - consumer warps in {2,4,6,8} times
  * coefficient ring stages in {2,3,4,6,8,12,16}, those whose shared memory
- * fits (for SFM_FP32F only stage counts that are multiples of the warps,
- * each with the single- and the paired-product kernel; for the panel modes
+ * fits (for SFM_FP32F only stage counts that are multiples of the warps;
+ * for the panel modes
  * 16-shot groups per task in {1, 2, 4, 8} times stages in {2, 3, 4, 6, 8}) -
  * steps the coupled system `nsteps` steps from rest with a zero source
  * twice (a state from sfm_set_initial or sfm_restore is left aside for
@@ -574,11 +574,7 @@ int sfm_last_launches(const sfm_handle* h, int* launches);
  *   key 3: consumer warps per stepping block (1..8), all precisions;
  *   key 4: coefficient ring stages per stepping block (2..16), all
  *          precisions (keys 3 and 4 override sfm_autotune's choice; for
- *          SFM_FP32F the stages are rounded up to a multiple of the warps);
- *   key 5: SFM_FP32F kernel: 0 = one factor product per warp at a time,
- *          1 = a warp's two owned blocks applied together (interleaved
- *          products; used on 48-wide blocks when the ring holds two stages
- *          per warp).  Both give bitwise the same traces.
+ *          SFM_FP32F the stages are rounded up to a multiple of the warps).
  * Errors: SFM_ERR_ARG for an unknown key or a value out of range.
  */
 int sfm_debug_set(sfm_handle* h, int key, long long value);

@@ -181,14 +181,6 @@ struct PolF32x2 {
 struct PolF32F : PolF32 {
     static constexpr bool factored = true;
     static constexpr int kind = 3;
-    static constexpr bool pair = false;
-};
-
-// The factored FP32 mode with a warp's two owned blocks applied together
-// (interleaved factor products): the same arithmetic, more registers per
-// thread; sfm_autotune picks between the two kernels.
-struct PolF32FP : PolF32F {
-    static constexpr bool pair = true;
 };
 
 }  // namespace sfm

@@ -141,7 +141,6 @@ struct sfm_ext {
     // stepping block shape per precision (FP64, FP32, FP32x2, FP32F): consumer
     // warps and coefficient ring stages; sfm_autotune overwrites these
     int ncw[4] = {8, 8, 8, 8}, nstage[4] = {4, 4, 4, 4};
-    bool f32f_pair = false;            // FP32F: the paired-product kernel (autotuned)
     int* d_piece_ptr = nullptr;
     int4* d_prec = nullptr;            // piece records (sfm::piece_records)
     int piece_grid = -1, piece_units = -1, piece_src = -1;
@@ -520,12 +519,6 @@ int sfm_debug_set(sfm_handle* h, int key, long long value) {
         for (int i = 0; i < 2; ++i) ext(h)->pnstage[i] = (int)value;
         return SFM_OK;
     }
-    if (key == 5) {
-        if (value < 0 || value > 1) return fail(h, SFM_ERR_ARG, "sfm_debug_set: key 5 takes 0 or 1");
-        ext(h)->f32f_pair = value == 1;
-        ext(h)->piece_grid = -1;
-        return SFM_OK;
-    }
     return fail(h, SFM_ERR_ARG, "sfm_debug_set: unknown key");
 }
 
@@ -611,23 +604,6 @@ static int prec_id(sfm::PolF32) { return SFM_FP32; }
 static int prec_id(sfm::PolF32x2) { return SFM_FP32X2; }
 static int prec_id(sfm::PolF32F) { return SFM_FP32F; }
 
-// The FP32F policy has two kernels, single and paired factor products
-// (same arithmetic); these pick the one the handle uses.
-template <class P>
-static int max_grid_of(sfm_handle* h, int ncw, size_t smem, int* g) {
-    if constexpr (std::is_same<P, sfm::PolF32F>::value)
-        if (ext(h)->f32f_pair) return sfm::step_max_grid<sfm::PolF32FP>(ncw, smem, g);
-    return sfm::step_max_grid<P>(ncw, smem, g);
-}
-
-template <class P>
-static cudaError_t launch_of(sfm_handle* h, const sfm::StepParams<typename P::S>& p, int grid,
-                             cudaStream_t st) {
-    if constexpr (std::is_same<P, sfm::PolF32F>::value)
-        if (ext(h)->f32f_pair) return sfm::launch_step<sfm::PolF32FP>(p, grid, st);
-    return sfm::launch_step<P>(p, grid, st);
-}
-
 // Grid of the persistent stepping kernel (co-resident blocks for the
 // chosen shape, at most one per level of work) and the per-block pieces.
 // src_off: host source offsets per (shot, subdomain), NULL for none (kind 0).
@@ -642,7 +618,7 @@ static int step_setup(sfm_handle* h, int nunits, const long long* src_off,
     // stages: the ring depth must be a multiple of the warp count
     if (P::factored) nstage = (nstage + ncw - 1) / ncw * ncw;
     int gmax = 0;
-    if (max_grid_of<P>(h, ncw, sfm::step_smem_bytes<P>(h->kmax, h->bmax, nstage), &gmax) != 0)
+    if (sfm::step_max_grid<P>(ncw, sfm::step_smem_bytes<P>(h->kmax, h->bmax, nstage), &gmax) != 0)
         return fail(h, SFM_ERR_ARG, "stepping: subdomain blocks too large for shared memory");
     long long levels = 0;
     for (int u = 0; u < nunits; ++u) levels += h->k[u % h->nsub];
@@ -932,7 +908,7 @@ static int run_impl(sfm_handle* h, double dt, int nsteps, const double* wavelet,
     p.rtab = h->d_rtab;
     if (rc != SFM_OK) { dfree(tmp64); return rc; }
     CK(h, cudaEventRecord(x->ev0, st));
-    cudaError_t e = launch_of<P>(h, p, grid, st);
+    cudaError_t e = sfm::launch_step<P>(p, grid, st);
     if (e != cudaSuccess) { dfree(tmp64); return cuda_fail(h, e, "step kernel launch"); }
     ++launches;
     CK(h, cudaEventRecord(x->ev1, st));
@@ -1312,38 +1288,25 @@ static int autotune_impl(sfm_handle* h, int nsteps, int* ncw_out, int* nstage_ou
     std::vector<double> tr((size_t)h->nshots * h->nrec * (nsteps + 1));
     double best = 1e300;
     int bn = ncw0, bs = nst0;
-    const bool pair0 = x->f32f_pair;
-    bool bp = pair0;
-    // FP32F: the paired kernel needs two ring stages per warp
-    const int nvar = std::is_same<P, sfm::PolF32F>::value ? 2 : 1;
-    for (int var = 0; var < nvar; ++var)
     for (int nc : kNcw) {
         for (int ns : kStage) {
             if (P::factored && ns % nc != 0) continue;   // see step_setup
-            if (var == 1 && ns < 2 * nc) continue;
-            x->f32f_pair = var == 1;
             int gmax = 0;
-            if (max_grid_of<P>(h, nc, sfm::step_smem_bytes<P>(h->kmax, h->bmax, ns), &gmax) != 0 ||
+            if (sfm::step_max_grid<P>(nc, sfm::step_smem_bytes<P>(h->kmax, h->bmax, ns), &gmax) != 0 ||
                 gmax < 1)
                 continue;
             x->ncw[id] = nc;
             x->nstage[id] = ns;
-            x->piece_grid = -1;                          // the grid may change with the kernel
             double ms = 0.0, ms2 = 0.0;
             int rc = run_impl<P>(h, 1.0, nsteps, wav.data(), tr.data(), 0, &ms);
             if (rc == SFM_OK) rc = run_impl<P>(h, 1.0, nsteps, wav.data(), tr.data(), 0, &ms2);
-            if (rc != SFM_OK) {
-                x->ncw[id] = ncw0; x->nstage[id] = nst0; x->f32f_pair = pair0;
-                return rc;
-            }
+            if (rc != SFM_OK) { x->ncw[id] = ncw0; x->nstage[id] = nst0; return rc; }
             ms = std::min(ms, ms2);
-            if (ms < best) { best = ms; bn = nc; bs = ns; bp = var == 1; }
+            if (ms < best) { best = ms; bn = nc; bs = ns; }
         }
     }
     x->ncw[id] = bn;
     x->nstage[id] = bs;
-    x->f32f_pair = bp;
-    x->piece_grid = -1;
     if (ncw_out) *ncw_out = bn;
     if (nstage_out) *nstage_out = bs;
     if (us_out) *us_out = best * 1e3 / nsteps;

@@ -157,7 +157,6 @@ SFM_INST(PolF64)
 SFM_INST(PolF32)
 SFM_INST(PolF32x2)
 SFM_INST(PolF32F)
-SFM_INST(PolF32FP)
 #undef SFM_INST
 
 // ---------------------------------------------------------------------------

@@ -396,81 +396,6 @@ __device__ __forceinline__ void factor_apply_any(int nt, const float* tiles, XF 
     else factor_apply(nt, tiles, xf, ef);
 }
 
-// Two independent factor products y_a = L_a (L_a^T x_a), y_b = L_b (L_b^T
-// x_b) by one warp, their instruction streams interleaved: each product is
-// a chain of shared loads, FMAs and shuffle reductions, so two chains in
-// flight hide each other's latencies.  Every lane sums in the same order as
-// factor_apply_nt, so the results are bitwise those of two single calls.
-template <int NT, class XA, class EA, class XB, class EB>
-__device__ __forceinline__ void factor_apply_nt_pair(const float* ta, XA xa, EA ea, const float* tb, XB xb,
-                                                     EB eb) {
-    const int lane = threadIdx.x & 31, r = lane >> 2, q = lane & 3;
-    const float* a0p = ta + r * 8 + 2 * q;
-    const float* b0p = tb + r * 8 + 2 * q;
-    float xra[NT], za0[NT], za1[NT], xrb[NT], zb0[NT], zb1[NT];
-#pragma unroll
-    for (int I = 0; I < NT; ++I) {
-        xra[I] = xa(8 * I + r);
-        xrb[I] = xb(8 * I + r);
-    }
-#pragma unroll
-    for (int J = 0; J < NT; ++J) {
-        float a0 = 0.f, a1 = 0.f, c0 = 0.f, c1 = 0.f;
-#pragma unroll
-        for (int I = J; I < NT; ++I) {
-            const float2 la = *reinterpret_cast<const float2*>(a0p + (I * (I + 1) / 2 + J) * 64);
-            const float2 lb = *reinterpret_cast<const float2*>(b0p + (I * (I + 1) / 2 + J) * 64);
-            a0 = fmaf(la.x, xra[I], a0);
-            a1 = fmaf(la.y, xra[I], a1);
-            c0 = fmaf(lb.x, xrb[I], c0);
-            c1 = fmaf(lb.y, xrb[I], c1);
-        }
-        za0[J] = a0; za1[J] = a1;
-        zb0[J] = c0; zb1[J] = c1;
-    }
-#pragma unroll
-    for (int o = 4; o < 32; o <<= 1) {
-#pragma unroll
-        for (int J = 0; J < NT; ++J) {
-            za0[J] += __shfl_xor_sync(0xffffffffu, za0[J], o);
-            za1[J] += __shfl_xor_sync(0xffffffffu, za1[J], o);
-            zb0[J] += __shfl_xor_sync(0xffffffffu, zb0[J], o);
-            zb1[J] += __shfl_xor_sync(0xffffffffu, zb1[J], o);
-        }
-    }
-    float va[NT], vb[NT];
-#pragma unroll
-    for (int I = 0; I < NT; ++I) {
-        float a0 = 0.f, a1 = 0.f, c0 = 0.f, c1 = 0.f;
-#pragma unroll
-        for (int J = 0; J <= I; ++J) {
-            const float2 la = *reinterpret_cast<const float2*>(a0p + (I * (I + 1) / 2 + J) * 64);
-            const float2 lb = *reinterpret_cast<const float2*>(b0p + (I * (I + 1) / 2 + J) * 64);
-            a0 = fmaf(la.x, za0[J], a0);
-            a1 = fmaf(la.y, za1[J], a1);
-            c0 = fmaf(lb.x, zb0[J], c0);
-            c1 = fmaf(lb.y, zb1[J], c1);
-        }
-        va[I] = a0 + a1;
-        vb[I] = c0 + c1;
-    }
-#pragma unroll
-    for (int o = 1; o < 4; o <<= 1) {
-#pragma unroll
-        for (int I = 0; I < NT; ++I) {
-            va[I] += __shfl_xor_sync(0xffffffffu, va[I], o);
-            vb[I] += __shfl_xor_sync(0xffffffffu, vb[I], o);
-        }
-    }
-    if (q == 0) {
-#pragma unroll
-        for (int I = 0; I < NT; ++I) {
-            ea(8 * I + r, va[I]);
-            eb(8 * I + r, vb[I]);
-        }
-    }
-}
-
 // Work of one block per time step: a list of pieces (unit, j0, j1), each a
 // contiguous range of levels of one (shot, subdomain) unit.  A piece streams
 // Gamma_j for j in [max(j0-1, 0), j1) (the extra level j0-1 gives phi_{j0-1},
@@ -674,95 +599,6 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
                 // its rows directly from the matvec.
                 const bool has_src = sof >= 0;
                 const float wf = (float)w;
-                if constexpr (P::pair) {
-                // A warp pairs the blocks it owns (j and j + ncw) when the
-                // ring holds two blocks per warp, so two factor products run
-                // interleaved; a block left over runs alone.
-                const bool pair = P::pair && nt == 6 && nstage >= 2 * ncw;
-                const float d2 = (float)dt2;
-                for (int half = 0; half < 2; ++half) {
-                    const int lo = half ? ja : jl;
-                    auto fU_of = [&](int j) { return reinterpret_cast<const float*>(sUs) + (j - jl) * bp; };
-                    auto fP_of = [&](int j) { return reinterpret_cast<float*>(sPhi) + (j - jl) * bp; };
-                    auto tl_of = [&](int st) { return reinterpret_cast<const float*>(stages) + (size_t)st * stage_elems; };
-                    // half 0: phi_j = L L^T Delta_j; half 1: a_j = Lh Lh^T psi_j
-                    // and the increment update of level j (Eq. 19)
-                    auto xf0 = [&](int j) {
-                        const float* fU = fU_of(j);
-                        return [fU, bp](int row) { return fU[bp + row] - fU[row]; };
-                    };
-                    auto ef0 = [&](int j) {
-                        float* fP = fP_of(j);
-                        return [fP](int row, float v) { fP[row] = v; };
-                    };
-                    auto xf1 = [&](int j) {
-                        const float* fP = fP_of(j);
-                        const float* sj = reinterpret_cast<const float*>(sSs) + (j - jl) * bp;
-                        return [fP, sj, bp, b, has_src, wf](int row) {
-                            float v = fP[row] - fP[row - bp];
-                            if (has_src && row < b) v += sj[row] * wf;
-                            return v;
-                        };
-                    };
-                    auto ef1 = [&](int j) {
-                        const float* fU = fU_of(j);
-                        const float* fD = reinterpret_cast<const float*>(sDs) + (j - jl) * bp;
-                        float* dUj = reinterpret_cast<float*>(dU) + j * b;
-                        float* Unj = reinterpret_cast<float*>(Un) + j * b;
-                        return [fU, fD, dUj, Unj, b, d2](int row, float v) {
-                            if (row < b) {
-                                const float d = fD[row] + d2 * v;
-                                dUj[row] = d;
-                                Unj[row] = fU[row] + d;
-                            }
-                        };
-                    };
-                    auto one = [&](int j, int st) {
-                        if (half == 0) factor_apply_any(nt, tl_of(st), xf0(j), ef0(j));
-                        else factor_apply_any(nt, tl_of(st), xf1(j), ef1(j));
-                    };
-                    int pj = -1, pst = 0;
-                    for (int j = lo; j < j1; ++j) {
-                        const int st = cst, owner = own;
-                        const unsigned ph = cph;
-                        if (++cst == nstage) { cst = 0; cph ^= 1u; }
-                        if (++own == ncw) own = 0;
-                        if (owner != warp) continue;
-                        if (!dead && !mbar_wait(full + st, ph, p.err, p.timeout_ns)) dead = true;
-                        if (dead) continue;
-                        if (pair && pj < 0) { pj = j; pst = st; continue; }
-                        if (pair) {
-                            if constexpr (P::pair) {
-                                if (half == 0)
-                                    factor_apply_nt_pair<6>(tl_of(pst), xf0(pj), ef0(pj), tl_of(st), xf0(j), ef0(j));
-                                else
-                                    factor_apply_nt_pair<6>(tl_of(pst), xf1(pj), ef1(pj), tl_of(st), xf1(j), ef1(j));
-                            }
-                            __syncwarp();
-                            if (lane == 0) { mbar_arrive(empty + pst); mbar_arrive(empty + st); }
-                            pj = -1;
-                        } else {
-                            one(j, st);
-                            __syncwarp();
-                            if (lane == 0) mbar_arrive(empty + st);
-                        }
-                    }
-                    if (pj >= 0 && !dead) {
-                        one(pj, pst);
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(empty + pst);
-                    }
-                    if (half == 0) {
-                        cbar(nct);
-                        // (2.1) publish face data [phi_1 + p_1 f]
-                        if (j0 == 0) {
-                            S* my_mail = mail + mo;
-                            for (int i = threadIdx.x; i < b; i += nct)
-                                P::st(my_mail + i, has_src ? P::add(sPhi[i], P::mul(sSs[i], w)) : sPhi[i]);
-                        }
-                    }
-                }
-                } else {
                 for (int half = 0; half < 2; ++half) {
                     const int lo = half ? ja : jl;
                     for (int j = lo; j < j1; ++j) {
@@ -812,7 +648,6 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
                                 P::st(my_mail + i, has_src ? P::add(sPhi[i], P::mul(sSs[i], w)) : sPhi[i]);
                         }
                     }
-                }
                 }
             } else {
             cbar(nct);

@@ -388,22 +388,3 @@ def test_config2_geometry_fp32f_matches_oracle(sfm, cfg2_layered):
     assert pipeline.rel_l2(got, ref) <= FP32F_GATE
     assert per_trace_errors(got, ref).max() <= FP32F_GATE
 
-
-def test_config2_geometry_paired_fp32f_kernel_is_bitwise_equal(sfm, cfg2_layered):
-    """48-wide blocks: the FP32F kernel that applies a warp's two owned
-    blocks together sums every product in the same order as the one that
-    applies them one at a time, so the traces are bitwise equal."""
-    p, rs, dt, w, ref = cfg2_layered
-    h = sfm.sfm_create(0)
-    try:
-        load_into(sfm, h, rs)
-        sfm.sfm_debug_set(h, 3, 4)
-        sfm.sfm_debug_set(h, 4, 8)
-        sfm.sfm_debug_set(h, 5, 0)
-        a, ms_a = sfm.sfm_run(h, sfm.SFM_FP32F, dt, p.nsteps, w, rs.nshots, rs.nrec)
-        sfm.sfm_debug_set(h, 5, 1)
-        b, ms_b = sfm.sfm_run(h, sfm.SFM_FP32F, dt, p.nsteps, w, rs.nshots, rs.nrec)
-    finally:
-        sfm.sfm_destroy(h)
-    print(f"FP32F single products {ms_a:.2f} ms, paired {ms_b:.2f} ms (4 warps, 8 stages)")
-    assert np.array_equal(a, b)
