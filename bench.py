@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--impl", default="sfm", choices=["sfm", "reference"])
     ap.add_argument("--nsteps", type=int, default=None, help="time steps per run (default: 4000)")
     ap.add_argument("--precision", default="auto",
-                    choices=["auto", "fp32f", "tf32x3", "tf32", "fp32", "fp32x2", "fp64"])
+                    choices=["auto", "fp32f", "tf32x3", "tf32", "fp32", "fp32fx2", "fp32x2", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched config-3 object of the headline line")
@@ -195,14 +195,16 @@ def algorithmic_bytes_per_step(p, nshots, receiver_numbers, word):
     per step the coefficient blocks (Gamma_1..k and Gammahat_2..k, each
     b(b+1)/2 numbers, packed symmetric or triangular factor), the face blocks
     H_f and the receiver rows (``receiver_numbers`` in all); per shot U and
-    delta read and written and the face data written and read back; ``word``
-    bytes per number."""
+    delta read and written and the face data written and read back.
+    ``word`` = (bytes per block number, bytes per other number)."""
+    wk, ws = word
     mf = face_modes(p)
     b = mf.sum(axis=1)
     k = np.asarray(p.k_sub)
-    coef = int(((2 * k - 1) * b * (b + 1) // 2).sum() + (mf * (mf + 1) // 2).sum() + receiver_numbers)
+    blocks = int(((2 * k - 1) * b * (b + 1) // 2).sum())
+    other = int((mf * (mf + 1) // 2).sum() + receiver_numbers)
     per_shot = int((4 * k * b + 2 * b).sum())
-    return (coef + nshots * per_shot) * word
+    return blocks * wk + (other + nshots * per_shot) * ws
 
 
 # ---------------------------------------------------------------------------
@@ -265,10 +267,12 @@ def reference_arm(args, rank, world):
 
 # ---------------------------------------------------------------------------
 
-MODES = ("fp32f", "tf32x3", "tf32", "fp32", "fp32x2")
-DTYPE = {"fp32f": "f32", "tf32x3": "tf32x3", "tf32": "tf32", "fp32": "f32", "fp32x2": "f32x2",
-         "fp64": "f64"}
-WORD = {"fp32f": 4, "tf32x3": 4, "tf32": 4, "fp32": 4, "fp32x2": 8, "fp64": 8}
+MODES = ("fp32f", "tf32x3", "tf32", "fp32", "fp32fx2", "fp32x2")
+DTYPE = {"fp32f": "f32", "tf32x3": "tf32x3", "tf32": "tf32", "fp32": "f32", "fp32fx2": "f32x2",
+         "fp32x2": "f32x2", "fp64": "f64"}
+# bytes per number: (S-fraction blocks or their factors, everything else)
+WORD = {"fp32f": (4, 4), "tf32x3": (4, 4), "tf32": (4, 4), "fp32": (4, 4), "fp32fx2": (4, 8),
+        "fp32x2": (8, 8), "fp64": (8, 8)}
 
 
 def build_workload(sfm, h, p, workload):
@@ -306,7 +310,8 @@ def measure_workload(sfm, torch, h, p, args, dt, nsteps, stream, local, dist, wo
     wav = torch.tensor(inputs.wavelet_samples(p, dt, nsteps), dtype=torch.float64, device="cuda")
     tr = torch.empty((nshots, nrec, nsteps + 1), dtype=torch.float64, device="cuda")
     modes = {"fp32f": sfm.SFM_FP32F, "tf32x3": sfm.SFM_TF32X3, "tf32": sfm.SFM_TF32,
-             "fp32": sfm.SFM_FP32, "fp32x2": sfm.SFM_FP32X2, "fp64": sfm.SFM_FP64}
+             "fp32": sfm.SFM_FP32, "fp32fx2": sfm.SFM_FP32FX2, "fp32x2": sfm.SFM_FP32X2,
+             "fp64": sfm.SFM_FP64}
 
     def run(prec):
         _, ms = sfm.sfm_run(h, prec, dt, nsteps, None, nshots, nrec,
@@ -328,7 +333,7 @@ def measure_workload(sfm, torch, h, p, args, dt, nsteps, stream, local, dist, wo
     if force:
         chosen = force
     else:
-        chosen = next(n for n in ("fp32f", "tf32x3", "fp32", "fp32x2", "fp64")
+        chosen = next(n for n in ("fp32f", "tf32x3", "fp32", "fp32fx2", "fp32x2", "fp64")
                       if errors.get(n) is not None and errors[n] <= GATE)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
     timed = {}
@@ -439,7 +444,8 @@ def main():
         nsteps = args.nsteps
     chosen, errors, timed, e2e_s, h2d, d2h = measure_workload(
         sfm, torch, h, p, args, dt, nsteps, stream, local, dist, world, args.warmup, args.steps, args.steps,
-        force=None if args.precision == "auto" else args.precision)
+        force=None if args.precision == "auto" else args.precision,
+        also=("fp32fx2",) if (args.workload == "cfg2" and not args.no_extra) else ())
     sfm.sfm_destroy(h)
     t = timed[chosen]
     ms = t["ms"]
@@ -484,8 +490,20 @@ def main():
            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
            "gpu_launches": t["launches"], "clocks": t["clocks"], "wall_s_timed": t["wall"]}
 
+    if "fp32fx2" in timed and chosen != "fp32fx2":
+        # the FP32-target mode (FP32 factor bytes, two-float state) on the
+        # same workload
+        tx = timed["fp32fx2"]
+        err = errors.get("fp32fx2")
+        out.setdefault("extra", {})["fp32fx2"] = {
+            "value": whole_job_rate(ncell * nsteps * (dt / dtf) * nshots, tx["ms"], world),
+            "ms_per_step": tx["ms"], "trace_err_vs_fp64": err,
+            "within_1e-5": err is not None and err <= 1e-5,
+            "roofline": roofline_of(p, "fp32fx2", tx, nsteps, pk, pk_kind, None),
+            "block_shape": tx["block_shape"], "clocks": tx["clocks"],
+            "gpu_launches": tx["launches"]}
     if args.workload == "cfg2" and world == 1 and not args.no_extra:
-        out["extra"] = {"cfg3": batched_extra(sfm, torch, args, local, pk, pk_kind)}
+        out.setdefault("extra", {})["cfg3"] = batched_extra(sfm, torch, args, local, pk, pk_kind)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:

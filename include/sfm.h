@@ -67,8 +67,13 @@ enum sfm_precision {
                                 FP32 factors and state                         */
     SFM_TF32 = 5,            /* as SFM_TF32X3 with single-word TF32 inputs
                                 (11 significant bits; deep ROMs diverge)       */
-    SFM_BF16 = 6             /* not built: sfm_run returns SFM_ERR_ARG (BF16's
+    SFM_BF16 = 6,            /* not built: sfm_run returns SFM_ERR_ARG (BF16's
                                 8-bit significand is coarser than TF32's)      */
+    SFM_FP32FX2 = 7          /* SFM_FP32F's FP32 Cholesky factors (the same
+                                coefficient bytes) with the state, the vectors
+                                of each product and its sums in SFM_FP32X2's
+                                two-float form: the factors' rounding is the
+                                only FP32 rounding                             */
 };
 
 /* flags for sfm_run */
@@ -182,9 +187,11 @@ int sfm_set_initial(sfm_handle* h, int nshots, int npairs, const int* pair_shot,
  * n = 0..nsteps-1 the right-hand sides of Eqs. 18-19 (with the source term
  * f_q(t_n)) are evaluated at t_n = n*dt and
  *     delta^{n+1} = delta^n + dt^2 a^n,  U^{n+1} = U^n + delta^{n+1}.
- *   precision      SFM_FP64, SFM_FP32, SFM_FP32X2 or SFM_FP32F (coefficients,
- *                  state, sums); SFM_FP32F first factors every block used
- *                  (SFM_ERR_NOT_SPD if one is not positive definite in FP64)
+ *   precision      SFM_FP64, SFM_FP32, SFM_FP32X2, SFM_FP32F or SFM_FP32FX2
+ *                  (one kernel over every shot), SFM_TF32X3 or SFM_TF32 (the
+ *                  multi-shot panels); the factored modes first factor every
+ *                  block used (SFM_ERR_NOT_SPD if one is not positive
+ *                  definite in FP64)
  *   wavelet        [nshots][nsteps] FP64 samples f_q(t_n)
  *   traces         [nshots][nrec][nsteps+1] FP64 output, d_r(t_n), n=0..nsteps
  *   flags          SFM_DEVICE_PTR: wavelet and traces are device pointers
@@ -325,6 +332,16 @@ typedef struct sfm_build_report {
  */
 int sfm_build_roms(sfm_handle* h, const int* m_sub, const int* k_sub, double sigma,
                    double cg_tol, sfm_build_report* rep);
+
+/* The same build with distinct finite shifts (Eq. 6's rational Krylov
+ * family): block j+1 of the subspace is (L + shifts[j-1])^{-1} applied to
+ * block j, j = 1..k_s-1, so the subspace holds F and (L + sigma_j)^{-1} F
+ * for every shift and the ROM interpolates the NtD map and its derivative
+ * at each of them.  shifts[nshifts] > 0, nshifts >= max k - 1; a subdomain
+ * with k_s levels uses the first k_s - 1.  Equal shifts give sfm_build_roms.
+ * Errors: as sfm_build_roms. */
+int sfm_build_roms_shifts(sfm_handle* h, const int* m_sub, const int* k_sub, const double* shifts,
+                          int nshifts, double cg_tol, sfm_build_report* rep);
 
 /* Algorithm 1 step 1.4 for point forces: a normalised Gaussian of the given
  * width (cut at 3 widths) around each point xyz[nshots][3] (metres); a node

@@ -235,7 +235,8 @@ extern "C" int sfm_set_model(sfm_handle* h, int nx, int ny, int nz, double hgrid
 // of d_preset, a full coefficient array on the device, and have no Krylov
 // basis for the projections of step 1.4).
 static int build_impl(sfm_handle* h, const int* m_sub, const int* k_sub, double sigma, double cg_tol,
-                      sfm_build_report* rep, const std::vector<char>* only, const double* d_preset) {
+                      sfm_build_report* rep, const std::vector<char>* only, const double* d_preset,
+                      const double* shifts = nullptr) {
     if (!h) return SFM_ERR_ARG;
     BuildState* B = bstate(h);
     if (!B || !B->d_c) return bfail(h, SFM_ERR_STATE, "sfm_build_roms: no model");
@@ -396,12 +397,15 @@ static int build_impl(sfm_handle* h, const int* m_sub, const int* k_sub, double 
         for (int j = 1; j < k; ++j) {
             double* Qj = c.V + (long long)(j - 1) * N * b;
             double* Wj = c.V + (long long)j * N * b;
+            // block j+1 = (L + sigma_j)^{-1} block j: one shift repeated, or
+            // the j-th of distinct shifts (Eq. 6)
+            const double sig = shifts ? shifts[j - 1] : sigma;
             // rhs = M^{1/2} Q_j
             sfm::bld::scale_kernel<<<grid_for((long long)ncolv * N), 256, 0, st>>>(Qj, sV, c.mass, rhs,
                                                                                    (long long)N * b, N,
                                                                                    b, S, 0);
             sfm::bld::cg_init_kernel<<<(int)ncolv, 256, 0, st>>>(rhs, Xc, Rc, Zc, Pc, c.mass, c.nxl, c.nyl,
-                                                                 c.nzl, B->h, sigma, b, rz, rr0);
+                                                                 c.nzl, B->h, sig, b, rz, rr0);
             BCK(h, cudaGetLastError());
             BCK(h, cudaMemcpyAsync(h_rr0.data(), rr0, ncolv * sizeof(double), cudaMemcpyDeviceToHost, st));
             int it = 0;
@@ -409,9 +413,9 @@ static int build_impl(sfm_handle* h, const int* m_sub, const int* k_sub, double 
             const int max_it = 20000;
             for (it = 1; it <= max_it; ++it) {
                 sfm::bld::op_kernel<<<(int)ncolv, 256, 0, st>>>(Pc, Qc, c.mass, c.nxl, c.nyl, c.nzl,
-                                                                B->h, sigma, b, 0, pq);
+                                                                B->h, sig, b, 0, pq);
                 sfm::bld::cg_update_kernel<<<(int)ncolv, 256, 0, st>>>(Xc, Rc, Zc, Pc, Qc, c.mass, c.nxl,
-                                                                       c.nyl, c.nzl, B->h, sigma, b,
+                                                                       c.nyl, c.nzl, B->h, sig, b,
                                                                        rz, pq, rz2, rr);
                 sfm::bld::cg_dir_kernel<<<(int)ncolv, 256, 0, st>>>(Pc, Zc, N, rz, rz2);
                 if (it % 8 == 0) {
@@ -586,6 +590,26 @@ static int build_impl(sfm_handle* h, const int* m_sub, const int* k_sub, double 
 extern "C" int sfm_build_roms(sfm_handle* h, const int* m_sub, const int* k_sub, double sigma,
                               double cg_tol, sfm_build_report* rep) {
     return build_impl(h, m_sub, k_sub, sigma, cg_tol, rep, nullptr, nullptr);
+}
+
+extern "C" int sfm_build_roms_shifts(sfm_handle* h, const int* m_sub, const int* k_sub,
+                                     const double* shifts, int nshifts, double cg_tol,
+                                     sfm_build_report* rep) {
+    if (!h) return SFM_ERR_ARG;
+    BuildState* B = bstate(h);
+    if (!B || !B->d_c) return bfail(h, SFM_ERR_STATE, "sfm_build_roms_shifts: no model");
+    if (!m_sub || !k_sub || !shifts || nshifts < 0)
+        return bfail(h, SFM_ERR_ARG, "sfm_build_roms_shifts: bad arguments");
+    const int nsub = ((int)B->xc.size() - 1) * ((int)B->yc.size() - 1) * ((int)B->zc.size() - 1);
+    int kmax = 1;
+    for (int s = 0; s < nsub; ++s) kmax = std::max(kmax, k_sub[s]);
+    if (nshifts < kmax - 1) return bfail(h, SFM_ERR_ARG, "sfm_build_roms_shifts: fewer shifts than kmax - 1");
+    for (int i = 0; i < nshifts; ++i)
+        if (!(shifts[i] > 0.0)) return bfail(h, SFM_ERR_ARG, "sfm_build_roms_shifts: shifts must be > 0");
+    // the single-shift argument only has to be valid; every solve takes its
+    // own shift
+    return build_impl(h, m_sub, k_sub, nshifts > 0 ? shifts[0] : 1.0, cg_tol, rep, nullptr, nullptr,
+                      shifts);
 }
 
 // Point weights of a set of points for every subdomain that holds one of

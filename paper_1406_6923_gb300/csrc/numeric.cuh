@@ -7,6 +7,10 @@
 //              the factored form stays positive semi-definite whatever the
 //              rounding of L, where FP32-rounded deep-ROM blocks (condition
 //              numbers up to ~1e14) turn indefinite and the leapfrog diverges.
+//   PolF32Fx2: FP32 Cholesky factors as in PolF32F (the same coefficient
+//              bytes), with the state, the vectors of the product and its
+//              sums in two-float form (below): the factors' rounding is the
+//              only FP32 rounding left.
 //   PolF32x2 : "two-float" numbers x = hi + lo (two FP32 words, ~48-bit
 //              significand) with FP32 arithmetic made exact by error-free
 //              transformations: Knuth's two-sum, the FMA two-product
@@ -53,6 +57,7 @@ struct PolF64 {
     static constexpr bool factored = false;
     using S = double;   // storage
     using C = double;   // value in registers / shared memory
+    using K = double;   // coefficient tile element
     static constexpr int kind = 0;
     __device__ static C ld(const S* p) { return *p; }
     // two consecutive elements in one 16-byte load (p 16-byte aligned)
@@ -86,6 +91,7 @@ struct PolF32 {
     static constexpr bool factored = false;
     using S = float;
     using C = float;
+    using K = float;
     static constexpr int kind = 1;
     __device__ static C ld(const S* p) { return *p; }
     __device__ static void ld2(const S* p, C& a, C& b) {
@@ -117,6 +123,7 @@ struct PolF32x2 {
     static constexpr bool factored = false;
     using S = float2;
     using C = df;
+    using K = float2;
     static constexpr int kind = 2;
     __device__ static C ld(const S* p) {
         const float2 v = *p;
@@ -181,6 +188,24 @@ struct PolF32x2 {
 struct PolF32F : PolF32 {
     static constexpr bool factored = true;
     static constexpr int kind = 3;
+};
+
+struct PolF32Fx2 : PolF32x2 {
+    static constexpr bool factored = true;
+    static constexpr int kind = 4;
+    using K = float;
+    // a += l x for a single-word factor element l: the two-float product
+    // with its low word's cross term dropped (l has none)
+    __device__ static void fma1(Acc& a, float l, C x) {
+        const float p = l * x.hi;
+        const float pe = fmaf(l, x.hi, -p);
+        const df t = two_sum(a.s, p);
+        a.s = t.hi;
+        a.e = a.e + fmaf(l, x.lo, t.lo + pe);
+    }
+    __device__ static Acc shfl_xor_acc(const Acc& a, int o) {
+        return {__shfl_xor_sync(0xffffffffu, a.s, o), __shfl_xor_sync(0xffffffffu, a.e, o)};
+    }
 };
 
 }  // namespace sfm

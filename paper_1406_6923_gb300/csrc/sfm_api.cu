@@ -59,9 +59,10 @@ cudaError_t upload(P*& d, const P* host, size_t count, cudaStream_t st) {
 template <typename T>
 struct Cache {
     T *coef = nullptr, *H = nullptr, *src = nullptr, *rrows = nullptr;
+    float* fcoef = nullptr;            // factored policies: FP32 factor tiles (coef unused)
     bool valid = false;
     void release() {
-        dfree(coef); dfree(H); dfree(src); dfree(rrows);
+        dfree(coef); dfree(fcoef); dfree(H); dfree(src); dfree(rrows);
         valid = false;
     }
 };
@@ -130,6 +131,7 @@ struct sfm_ext {
     Cache<double> c64;
     Cache<float2> c2;
     Cache<float> c32f;                 // factored FP32 coefficients
+    Cache<float2> c2f;                 // factored FP32 coefficients, two-float state
     RunBufs<float> r32;
     RunBufs<double> r64;
     RunBufs<float2> r2;
@@ -140,7 +142,7 @@ struct sfm_ext {
     int skip_arrive = -1;
     // stepping block shape per precision (FP64, FP32, FP32x2, FP32F): consumer
     // warps and coefficient ring stages; sfm_autotune overwrites these
-    int ncw[4] = {8, 8, 8, 8}, nstage[4] = {4, 4, 4, 4};
+    int ncw[8] = {8, 8, 8, 8, 8, 8, 8, 8}, nstage[8] = {4, 4, 4, 4, 4, 4, 4, 4};
     int* d_piece_ptr = nullptr;
     int4* d_prec = nullptr;            // piece records (sfm::piece_records)
     int piece_grid = -1, piece_units = -1, piece_src = -1;
@@ -159,6 +161,7 @@ static void invalidate(sfm_handle* h) {
     ext(h)->c64.release();
     ext(h)->c2.release();
     ext(h)->c32f.release();
+    ext(h)->c2f.release();
 }
 
 extern "C" {
@@ -198,7 +201,7 @@ int sfm_destroy(sfm_handle* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     sfm_ext* x = ext(h);
     if (x) {
-        x->c32.release(); x->c64.release(); x->c2.release(); x->c32f.release();
+        x->c32.release(); x->c64.release(); x->c2.release(); x->c32f.release(); x->c2f.release();
         x->r32.release(); x->r64.release(); x->r2.release();
         x->pc.release(); x->pb.release();
         dfree(x->d_ustep);
@@ -509,13 +512,13 @@ int sfm_debug_set(sfm_handle* h, int key, long long value) {
     if (key == 2) { ext(h)->skip_arrive = (int)value; return SFM_OK; }
     if (key == 3) {
         if (value < 1 || value > 8) return fail(h, SFM_ERR_ARG, "sfm_debug_set: consumer warps 1..8");
-        for (int i = 0; i < 4; ++i) ext(h)->ncw[i] = (int)value;
+        for (int i = 0; i < 8; ++i) ext(h)->ncw[i] = (int)value;
         for (int i = 0; i < 2; ++i) ext(h)->pncw[i] = (int)value;
         return SFM_OK;
     }
     if (key == 4) {
         if (value < 2 || value > 16) return fail(h, SFM_ERR_ARG, "sfm_debug_set: ring stages 2..16");
-        for (int i = 0; i < 4; ++i) ext(h)->nstage[i] = (int)value;
+        for (int i = 0; i < 8; ++i) ext(h)->nstage[i] = (int)value;
         for (int i = 0; i < 2; ++i) ext(h)->pnstage[i] = (int)value;
         return SFM_OK;
     }
@@ -557,6 +560,7 @@ static Cache<double>& cache_of(sfm_handle* h, sfm::PolF64) { return ext(h)->c64;
 static Cache<float>& cache_of(sfm_handle* h, sfm::PolF32) { return ext(h)->c32; }
 static Cache<float2>& cache_of(sfm_handle* h, sfm::PolF32x2) { return ext(h)->c2; }
 static Cache<float>& cache_of(sfm_handle* h, sfm::PolF32F) { return ext(h)->c32f; }
+static Cache<float2>& cache_of(sfm_handle* h, sfm::PolF32Fx2) { return ext(h)->c2f; }
 template <typename T>
 static RunBufs<T>& bufs_of(sfm_handle* h);
 template <>
@@ -573,7 +577,8 @@ static int prepare(sfm_handle* h) {
     if (c.valid) return SFM_OK;
     c.release();
     cudaStream_t st = h->stream;
-    CK(h, dalloc(c.coef, (size_t)h->ntcoef));
+    if constexpr (P::factored) CK(h, dalloc(c.fcoef, (size_t)h->ntcoef));
+    else CK(h, dalloc(c.coef, (size_t)h->ntcoef));
     CK(h, dalloc(c.H, (size_t)h->nH));
     CK(h, dalloc(c.src, (size_t)h->nsrc));
     CK(h, dalloc(c.rrows, (size_t)h->nrrow));
@@ -581,7 +586,7 @@ static int prepare(sfm_handle* h) {
     if constexpr (P::factored) {
         CK(h, cudaMemsetAsync(ext(h)->d_bad, 0, sizeof(int), st));
         CK(h, sfm::launch_factor_tiles(h->d_coef64, h->d_coef_off, h->d_tcoef_off, h->d_b, h->d_k,
-                                       h->nsub, h->kmax, c.coef, ext(h)->d_bad, st));
+                                       h->nsub, h->kmax, c.fcoef, ext(h)->d_bad, st));
         CK(h, cudaMemcpyAsync(&bad, ext(h)->d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
     } else {
         CK(h, sfm::launch_pack_tiles<P>(h->d_coef64, h->d_coef_off, h->d_tcoef_off, h->d_b, h->d_k,
@@ -603,6 +608,7 @@ static int prec_id(sfm::PolF64) { return SFM_FP64; }
 static int prec_id(sfm::PolF32) { return SFM_FP32; }
 static int prec_id(sfm::PolF32x2) { return SFM_FP32X2; }
 static int prec_id(sfm::PolF32F) { return SFM_FP32F; }
+static int prec_id(sfm::PolF32Fx2) { return SFM_FP32FX2; }
 
 // Grid of the persistent stepping kernel (co-resident blocks for the
 // chosen shape, at most one per level of work) and the per-block pieces.
@@ -643,9 +649,11 @@ static int step_setup(sfm_handle* h, int nunits, const long long* src_off,
     p.nstage = nstage;
     p.stage_v4 = 0;
     if (P::factored) {
+        // 16-byte staging copies when every width is a whole number of them
+        const int epv = (int)(16 / sizeof(typename P::S));
         p.stage_v4 = 1;
         for (int s = 0; s < h->nsub; ++s)
-            if (h->b[s] % 4 != 0) p.stage_v4 = 0;
+            if (h->b[s] % epv != 0) p.stage_v4 = 0;
     }
     p.piece_ptr = x->d_piece_ptr;
     p.prec = x->d_prec;
@@ -888,6 +896,7 @@ static int run_impl(sfm_handle* h, double dt, int nsteps, const double* wavelet,
     p.nsub = h->nsub; p.nshots = h->nshots; p.nunits = h->nshots * h->nsub; p.nsteps = nsteps;
     p.kmax = h->kmax; p.bmax = h->bmax;
     p.sub_b = h->d_b; p.sub_k = h->d_k; p.coef_off = h->d_tcoef_off; p.coef = c.coef;
+    p.fcoef = c.fcoef;
     p.face_off = h->d_face_off; p.nbr = h->d_nbr; p.H_off = h->d_H_off; p.H = c.H;
     p.state_off = h->d_state_off; p.state_stride = h->nstate;
     for (int i = 0; i < 4; ++i) p.U[i] = r.U[i];
@@ -1238,6 +1247,8 @@ extern "C" int sfm_run(sfm_handle* h, int precision, double dt, int nsteps, cons
         rc = run_impl<sfm::PolF32x2>(h, dt, nsteps, wavelet, traces, flags, kernel_ms);
     else if (precision == SFM_FP32F)
         rc = run_impl<sfm::PolF32F>(h, dt, nsteps, wavelet, traces, flags, kernel_ms);
+    else if (precision == SFM_FP32FX2)
+        rc = run_impl<sfm::PolF32Fx2>(h, dt, nsteps, wavelet, traces, flags, kernel_ms);
     else if (precision == SFM_TF32X3 || precision == SFM_TF32)
         rc = run_panel_impl(h, panel_mode_of(precision), dt, nsteps, wavelet, traces, flags, kernel_ms);
     else if (precision == SFM_BF16)
@@ -1373,6 +1384,8 @@ extern "C" int sfm_autotune(sfm_handle* h, int precision, int nsteps, int* ncw, 
         rc = autotune_impl<sfm::PolF32x2>(h, nsteps, ncw, nstage, us_per_step);
     else if (precision == SFM_FP32F)
         rc = autotune_impl<sfm::PolF32F>(h, nsteps, ncw, nstage, us_per_step);
+    else if (precision == SFM_FP32FX2)
+        rc = autotune_impl<sfm::PolF32Fx2>(h, nsteps, ncw, nstage, us_per_step);
     else if (precision == SFM_TF32X3 || precision == SFM_TF32)
         rc = autotune_panel(h, panel_mode_of(precision), nsteps, ncw, nstage, us_per_step);
     else
@@ -1462,7 +1475,7 @@ extern "C" int sfm_checkpoint(sfm_handle* h, void* buf, size_t* bytes) {
         dfree(dDx);
     } else if (x->ck_prec == SFM_FP64)
         e = fetch_state(x->r64.U[slot], x->r64.dU, n, h->stream, U, dU);
-    else if (x->ck_prec == SFM_FP32X2)
+    else if (x->ck_prec == SFM_FP32X2 || x->ck_prec == SFM_FP32FX2)
         e = fetch_state(x->r2.U[slot], x->r2.dU, n, h->stream, U, dU);
     else
         e = fetch_state(x->r32.U[slot], x->r32.dU, n, h->stream, U, dU);

@@ -25,6 +25,8 @@ struct StepParams {
     const int* sub_k;            // [nsub]
     const long long* coef_off;   // [nsub] -> per level j: Gamma_j tiles, Gammahat_j tiles
     const T* coef;               // 8x8-tile packed upper triangles (see pack_tiles_kernel)
+    const float* fcoef;          // factored policies: FP32 lower Cholesky factor tiles
+                                 // (see factor_tiles_kernel), same offsets
     const int* face_off;         // [nsub*7] start of face f inside the b-vector
     const int* nbr;              // [nsub*6]
     const long long* H_off;      // [nsub*6] -> m_f*m_f block, or -1

@@ -157,6 +157,7 @@ SFM_INST(PolF64)
 SFM_INST(PolF32)
 SFM_INST(PolF32x2)
 SFM_INST(PolF32F)
+SFM_INST(PolF32Fx2)
 #undef SFM_INST
 
 // ---------------------------------------------------------------------------
@@ -342,6 +343,7 @@ SFM_INST2(PolF64)
 SFM_INST2(PolF32)
 SFM_INST2(PolF32x2)
 SFM_INST2(PolF32F)
+SFM_INST2(PolF32Fx2)
 #undef SFM_INST2
 
 // ---------------------------------------------------------------------------

@@ -396,6 +396,75 @@ __device__ __forceinline__ void factor_apply_any(int nt, const float* tiles, XF 
     else factor_apply(nt, tiles, xf, ef);
 }
 
+// The product of factor_apply for two-float vectors (PolF32Fx2): the same
+// lanes, tile loads and summation order, with every sum compensated
+// (PolF32Fx2::fma1 per product, two-float butterflies), so that the FP32
+// factor elements are the only rounded operands.  NT is the largest tile
+// count; nt <= NT the block's.
+template <int NT, class XF, class EF>
+__device__ __forceinline__ void factor_apply2_nt(int nt, const float* tiles, XF xf, EF ef) {
+    using P = PolF32Fx2;
+    const int lane = threadIdx.x & 31, r = lane >> 2, q = lane & 3;
+    const float* t0 = tiles + r * 8 + 2 * q;
+    df xr[NT], z0[NT], z1[NT];
+#pragma unroll
+    for (int I = 0; I < NT; ++I) xr[I] = (I < nt) ? xf(8 * I + r) : df{0.f, 0.f};
+#pragma unroll
+    for (int J = 0; J < NT; ++J) {
+        P::Acc a0 = P::acc0(), a1 = P::acc0();
+        if (J < nt) {
+#pragma unroll
+            for (int I = J; I < NT; ++I) {
+                if (I < nt) {
+                    const float2 l =
+                        *reinterpret_cast<const float2*>(t0 + (I * (I + 1) / 2 + J) * 64);
+                    P::fma1(a0, l.x, xr[I]);
+                    P::fma1(a1, l.y, xr[I]);
+                }
+            }
+            // the two-sum is exact, so both lanes of each exchange get the
+            // same merged value and the whole column group agrees
+#pragma unroll
+            for (int o = 4; o < 32; o <<= 1) {
+                a0 = P::merge(a0, P::shfl_xor_acc(a0, o));
+                a1 = P::merge(a1, P::shfl_xor_acc(a1, o));
+            }
+        }
+        z0[J] = P::get(a0);
+        z1[J] = P::get(a1);
+    }
+#pragma unroll
+    for (int I = 0; I < NT; ++I) {
+        if (I < nt) {
+            P::Acc a0 = P::acc0(), a1 = P::acc0();
+#pragma unroll
+            for (int J = 0; J <= I; ++J) {
+                const float2 l = *reinterpret_cast<const float2*>(t0 + (I * (I + 1) / 2 + J) * 64);
+                P::fma1(a0, l.x, z0[J]);
+                P::fma1(a1, l.y, z1[J]);
+            }
+            P::Acc a = P::merge(a0, a1);
+            a = P::merge(a, P::shfl_xor_acc(a, 1));
+            a = P::merge(a, P::shfl_xor_acc(a, 2));
+            if (q == 0) ef(8 * I + r, P::get(a));
+        }
+    }
+}
+
+template <class XF, class EF>
+__device__ __forceinline__ void factor_apply2_any(int nt, const float* tiles, XF xf, EF ef) {
+    if (nt == 6) factor_apply2_nt<6>(6, tiles, xf, ef);
+    else factor_apply2_nt<8>(nt, tiles, xf, ef);
+}
+
+// Coefficient tiles the producer streams: the packed blocks, or the factor
+// tiles for the factored policies.
+template <class P>
+__device__ __forceinline__ const typename P::K* coef_base(const StepParams<typename P::S>& p) {
+    if constexpr (P::factored) return p.fcoef;
+    else return p.coef;
+}
+
 // Work of one block per time step: a list of pieces (unit, j0, j1), each a
 // contiguous range of levels of one (shot, subdomain) unit.  A piece streams
 // Gamma_j for j in [max(j0-1, 0), j1) (the extra level j0-1 gives phi_{j0-1},
@@ -409,11 +478,12 @@ template <class P>
 __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typename P::S> p) {
     using S = typename P::S;
     using C = typename P::C;
+    using K = typename P::K;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int ncw = p.ncw, nct = ncw * 32, nstage = p.nstage;
     const int bpm = ((p.bmax + 7) / 8) * 8;
     const int stage_elems = (int)(sym_tiles(p.bmax) * 64);
-    S* stages = reinterpret_cast<S*>(smem_raw);
+    K* stages = reinterpret_cast<K*>(smem_raw);
     // Per-piece staging: the factored path double-buffers the state,
     // increment and source rows (set 1 at +SU / +SD) so the next piece loads
     // while the current one computes.
@@ -461,7 +531,7 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
                 const int b = r1.x & 255;
                 const int nt = (b + 7) >> 3;
                 const long long ltile = 2LL * (nt * (nt + 1) / 2) * 64;
-                const unsigned bytes = (unsigned)((ltile / 2) * sizeof(S));
+                const unsigned bytes = (unsigned)((ltile / 2) * sizeof(K));
                 const long long T0 = p.coef_off[s];
                 const int jl = j0 > 0 ? j0 - 1 : 0, ja = j0 > 1 ? j0 : 1;
                 const int nblk = piece_blocks(j0, j1);
@@ -474,7 +544,7 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
                     const long long off = (m < j1 - jl) ? T0 + (long long)(jl + m) * ltile
                                                         : T0 + (long long)(ja + m - (j1 - jl)) * ltile + ltile / 2;
                     mbar_expect_tx(full + st, bytes);
-                    bulk_g2s(stages + (size_t)st * stage_elems, p.coef + off, bytes, full + st);
+                    bulk_g2s(stages + (size_t)st * stage_elems, coef_base<P>(p) + off, bytes, full + st);
                     if (++st == nstage) { st = 0; ph ^= 1u; }
                 }
             }
@@ -501,6 +571,7 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
     bool dead = false;
     // factored path: issue the copies of piece pcx into staging set `set`
     // (one cp.async group per call; zero padding written directly)
+    constexpr int EPV = (int)(16 / sizeof(S));   // state elements per 16-byte copy
     auto stage = [&](int pcx, int set, const S* Ubuf) {
         const int4 a0 = prec(pcx, 0), a1 = prec(pcx, 1);
         const int xj0 = a0.z, xj1 = a0.w, xb = a1.x & 255, xk = a1.x >> 8;
@@ -511,24 +582,24 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
         C* xD = sD + set * SD;
         C* xS = sSrc + set * SD;
         if (p.stage_v4) {
-            // every width a multiple of 4: 16-byte copies, zero padding from
-            // b to the tile width and for level k (if reached)
+            // every width a multiple of EPV: 16-byte copies, zero padding
+            // from b to the tile width and for level k (if reached)
             for (int lj = warp; lj <= xnl; lj += ncw) {
                 const int j = xjl + lj;
-                for (int i = 4 * lane; i < xbp; i += 128) {
+                for (int i = EPV * lane; i < xbp; i += 32 * EPV) {
                     if (j < xk && i < xb) cp_async<16>(xU + lj * xbp + i, Ubuf + xso + j * xb + i);
                     else *reinterpret_cast<float4*>(xU + lj * xbp + i) = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
             }
             for (int lj = xja - xjl + warp; lj < xnl; lj += ncw) {
                 const int j = xjl + lj;
-                for (int i = 4 * lane; i < xb; i += 128)
+                for (int i = EPV * lane; i < xb; i += 32 * EPV)
                     cp_async<16>(xD + lj * xbp + i, p.dU + xso + j * xb + i);
             }
             if (xsof >= 0) {
                 for (int lj = warp; lj < xnl; lj += ncw) {
                     const int j = xjl + lj;
-                    for (int i = 4 * lane; i < xb; i += 128)
+                    for (int i = EPV * lane; i < xb; i += 32 * EPV)
                         cp_async<16>(xS + lj * xbp + i, p.src + xsof + j * xb + i);
                 }
             }
@@ -598,7 +669,6 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
                 // the same way and applies the increment update (Eq. 19) to
                 // its rows directly from the matvec.
                 const bool has_src = sof >= 0;
-                const float wf = (float)w;
                 for (int half = 0; half < 2; ++half) {
                     const int lo = half ? ja : jl;
                     for (int j = lo; j < j1; ++j) {
@@ -610,31 +680,61 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
                         if (!dead && !mbar_wait(full + st, ph, p.err, p.timeout_ns)) dead = true;
                         if (dead) continue;
                         const float* tl = reinterpret_cast<const float*>(stages) + (size_t)st * stage_elems;
-                        const float* fU = reinterpret_cast<const float*>(sUs) + (j - jl) * bp;
-                        float* fP = reinterpret_cast<float*>(sPhi) + (j - jl) * bp;
-                        if (half == 0) {
-                            factor_apply_any(nt, tl,
-                                         [&](int row) { return fU[bp + row] - fU[row]; },
-                                         [&](int row, float v) { fP[row] = v; });
+                        if constexpr (sizeof(C) == sizeof(float)) {
+                            const float wf = w;
+                            const float* fU = reinterpret_cast<const float*>(sUs) + (j - jl) * bp;
+                            float* fP = reinterpret_cast<float*>(sPhi) + (j - jl) * bp;
+                            if (half == 0) {
+                                factor_apply_any(nt, tl,
+                                             [&](int row) { return fU[bp + row] - fU[row]; },
+                                             [&](int row, float v) { fP[row] = v; });
+                            } else {
+                                const float* sj = reinterpret_cast<const float*>(sSs) + (j - jl) * bp;
+                                const float* fD = reinterpret_cast<const float*>(sDs) + (j - jl) * bp;
+                                float* dUj = reinterpret_cast<float*>(dU) + j * b;
+                                float* Unj = reinterpret_cast<float*>(Un) + j * b;
+                                const float d2 = (float)dt2;
+                                factor_apply_any(nt, tl,
+                                             [&](int row) {
+                                                 float v = fP[row] - fP[row - bp];
+                                                 if (has_src && row < b) v += sj[row] * wf;
+                                                 return v;
+                                             },
+                                             [&](int row, float v) {
+                                                 if (row < b) {
+                                                     const float d = fD[row] + d2 * v;
+                                                     dUj[row] = d;
+                                                     Unj[row] = fU[row] + d;
+                                                 }
+                                             });
+                            }
                         } else {
-                            const float* sj = reinterpret_cast<const float*>(sSs) + (j - jl) * bp;
-                            const float* fD = reinterpret_cast<const float*>(sDs) + (j - jl) * bp;
-                            float* dUj = reinterpret_cast<float*>(dU) + j * b;
-                            float* Unj = reinterpret_cast<float*>(Un) + j * b;
-                            const float d2 = (float)dt2;
-                            factor_apply_any(nt, tl,
-                                         [&](int row) {
-                                             float v = fP[row] - fP[row - bp];
-                                             if (has_src && row < b) v += sj[row] * wf;
-                                             return v;
-                                         },
-                                         [&](int row, float v) {
-                                             if (row < b) {
-                                                 const float d = fD[row] + d2 * v;
-                                                 dUj[row] = d;
-                                                 Unj[row] = fU[row] + d;
-                                             }
-                                         });
+                            // two-float state, FP32 factor tiles (PolF32Fx2)
+                            const C* fU = sUs + (j - jl) * bp;
+                            C* fP = sPhi + (j - jl) * bp;
+                            if (half == 0) {
+                                factor_apply2_any(nt, tl,
+                                                  [&](int row) { return P::sub(fU[bp + row], fU[row]); },
+                                                  [&](int row, C v) { fP[row] = v; });
+                            } else {
+                                const C* sj = sSs + (j - jl) * bp;
+                                const C* fD = sDs + (j - jl) * bp;
+                                S* dUj = dU + j * b;
+                                S* Unj = Un + j * b;
+                                factor_apply2_any(nt, tl,
+                                                  [&](int row) {
+                                                      C v = P::sub(fP[row], fP[row - bp]);
+                                                      if (has_src && row < b) v = P::add(v, P::mul(sj[row], w));
+                                                      return v;
+                                                  },
+                                                  [&](int row, C v) {
+                                                      if (row < b) {
+                                                          const C d = P::add(fD[row], P::mul(dt2, v));
+                                                          P::st(dUj + row, d);
+                                                          P::st(Unj + row, P::add(fU[row], d));
+                                                      }
+                                                  });
+                            }
                         }
                         __syncwarp();
                         if (lane == 0) mbar_arrive(empty + st);
@@ -792,7 +892,7 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
 template <class P>
 size_t step_smem_bytes(int kmax, int bmax, int nstage) {
     const size_t bp = (size_t)((bmax + 7) / 8) * 8;
-    size_t bytes = (size_t)nstage * sym_tiles(bmax) * 64 * sizeof(typename P::S);
+    size_t bytes = (size_t)nstage * sym_tiles(bmax) * 64 * sizeof(typename P::K);
     const size_t nset = P::factored ? 2 : 1;
     bytes += sizeof(typename P::C) *
              (nset * (size_t)(kmax + 1) * bp + (nset + 1 + (P::factored ? nset : 0)) * (size_t)kmax * bp);

@@ -31,6 +31,7 @@ SFM_FP32F = 3
 SFM_TF32X3 = 4
 SFM_TF32 = 5
 SFM_BF16 = 6
+SFM_FP32FX2 = 7
 
 SFM_DEVICE_PTR = 1
 SFM_ENERGY = 2
@@ -44,7 +45,7 @@ EXPORTS = ["sfm_create", "sfm_destroy", "sfm_last_error", "sfm_set_stream", "sfm
            "sfm_cut_depth", "sfm_checkpoint", "sfm_restore", "sfm_run_report",
            "sfm_net_create", "sfm_net_destroy", "sfm_net_last_error", "sfm_net_params",
            "sfm_net_grad", "sfm_net_adam", "sfm_net_forward", "sfm_raw_encode",
-           "sfm_net_fit_decoder", "sfm_net_decode", "sfm_ntd_error", "sfm_build_roms_surrogate"]
+           "sfm_net_fit_decoder", "sfm_net_decode", "sfm_ntd_error", "sfm_build_roms_surrogate", "sfm_build_roms_shifts"]
 
 
 class sfm_build_report(C.Structure):
@@ -129,6 +130,7 @@ def load(path=LIB_PATH):
         "sfm_net_fit_decoder": (_i, [_p, _i, _i, _p, _i, _i, C.c_ulonglong, _p]),
         "sfm_net_decode": (_i, [_p, _p, _i, _p]),
         "sfm_ntd_error": (_i, [_i, _i, _i, _i, _p, _p, _i, _dp, _dp]),
+        "sfm_build_roms_shifts": (_i, [_p, _ip, _ip, _dp, _i, C.c_double, C.POINTER(sfm_build_report)]),
         "sfm_build_roms_surrogate": (_i, [_p, _p, _ip, _ip, C.c_double, C.c_double, C.c_double, _ip,
                                           C.POINTER(sfm_surrogate_report), C.POINTER(sfm_build_report)]),
     }
@@ -329,6 +331,16 @@ def sfm_build_roms(h, m_sub, k_sub, sigma, cg_tol=1e-14):
     k, kp = _iarr(k_sub)
     rep = sfm_build_report()
     _check(h, load().sfm_build_roms(h, mp, kp, float(sigma), float(cg_tol), C.byref(rep)))
+    return {f: getattr(rep, f) for f, _ in sfm_build_report._fields_}
+
+
+def sfm_build_roms_shifts(h, m_sub, k_sub, shifts, cg_tol=1e-14):
+    """The offline build with distinct Krylov shifts (Eq. 6)."""
+    m, mp = _iarr(m_sub)
+    k, kp = _iarr(k_sub)
+    sh, sp = _darr(np.asarray(shifts, dtype=np.float64))
+    rep = sfm_build_report()
+    _check(h, load().sfm_build_roms_shifts(h, mp, kp, sp, len(sh), float(cg_tol), C.byref(rep)))
     return {f: getattr(rep, f) for f, _ in sfm_build_report._fields_}
 
 

@@ -44,10 +44,13 @@ def test_config2_bytes_per_step():
     assert rec == npairs * 16 * 48
     per_sub = 31 * 48 * 49 // 2 + 6 * 8 * 9 // 2 + 4 * 16 * 48 + 2 * 48
     want = (512 * per_sub + rec) * 4
-    assert bench.algorithmic_bytes_per_step(p, 1, rec, 4) == want == 88338432
-    assert bench.algorithmic_bytes_per_step(p, 1, rec, 8) == 2 * want
+    assert bench.algorithmic_bytes_per_step(p, 1, rec, (4, 4)) == want == 88338432
+    assert bench.algorithmic_bytes_per_step(p, 1, rec, (8, 8)) == 2 * want
     # more shots add only the per-shot state
-    assert (bench.algorithmic_bytes_per_step(p, 3, rec, 4) - want) == 2 * 512 * (4 * 16 * 48 + 2 * 48) * 4
+    assert (bench.algorithmic_bytes_per_step(p, 3, rec, (4, 4)) - want) == 2 * 512 * (4 * 16 * 48 + 2 * 48) * 4
+    # FP32 factors with a two-float state: only the blocks stay at 4 bytes
+    blocks = 512 * 31 * 48 * 49 // 2
+    assert bench.algorithmic_bytes_per_step(p, 1, rec, (4, 8)) == 2 * want - 4 * blocks
 
 
 @pytest.mark.slow

@@ -164,3 +164,34 @@ def test_builder_full_config2_sampled_against_oracle(sfm):
             a = sfrac.transfer_sfraction(list(G), list(H), lam)
             r = sfrac.transfer_sfraction(list(Gam[s]), list(Gh[s]), lam)
             assert np.linalg.norm(a - r) / np.linalg.norm(r) < 1e-6, (s, lam)
+
+
+def test_builder_with_distinct_shifts_matches_oracle(sfm):
+    """Distinct finite shifts (Eq. 6): the GPU build against the oracle's
+    build with the same three shifts, coefficient by coefficient and through
+    the transfer function, which interpolates the subdomain's NtD map at
+    every shift."""
+    p = inputs.small_problem(ncell=(10, 9, 8), cuts=([0, 5, 10], [0, 4, 9], [0, 4, 8]), m=3, k=4,
+                             model="random")
+    base = p.sigma
+    shifts = [0.05 * base, 0.6 * base, 4.0 * base]
+    p.sigma = shifts
+    rs = pipeline.build(p)
+    h = sfm.sfm_create(0)
+    try:
+        sfm.sfm_set_model(h, p.c, p.h, p.xcuts, p.ycuts, p.zcuts)
+        rep = sfm.sfm_build_roms_shifts(h, p.m_sub, p.k_sub, shifts)
+        got = _split(sfm.sfm_get_coeffs(h), rs)
+    finally:
+        sfm.sfm_destroy(h)
+    assert rep["cg_residual_max"] < 1e-13
+    rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
+    for s in range(rs.nsub):
+        G, Gh = got[s]
+        for j in range(rs.k[s]):
+            assert rel(Gh[j], rs.Gammahat[s][j]) < 1e-8, (s, j)
+            assert rel(G[j], rs.Gamma[s][j]) < 1e-7, (s, j)
+        for lam in (shifts[0], shifts[2], 0.3 * base * (1 + 1j)):
+            a = sfrac.transfer_sfraction(list(G), list(Gh), lam)
+            r = sfrac.transfer_sfraction(list(rs.Gamma[s]), list(rs.Gammahat[s]), lam)
+            assert rel(a, r) < 1e-9, (s, lam)

@@ -65,9 +65,10 @@ def test_restored_run_continues_bitwise(sfm, small, prec_name):
     np.testing.assert_array_equal(second, whole[..., N:])
 
 
-def test_restored_two_float_run_continues(sfm, small):
+@pytest.mark.parametrize("prec_name", ["SFM_FP32X2", "SFM_FP32FX2"])
+def test_restored_two_float_run_continues(sfm, small, prec_name):
     p, rs, dt, w = small
-    whole, first, second, _ = _split_run(sfm, rs, dt, w, sfm.SFM_FP32X2)
+    whole, first, second, _ = _split_run(sfm, rs, dt, w, getattr(sfm, prec_name))
     assert pipeline.rel_l2(second, whole[..., N:]) < 1e-13
 
 

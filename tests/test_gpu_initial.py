@@ -96,6 +96,12 @@ def test_initial_state_fp32x2_matches_oracle(sfm, initial):
     assert pipeline.rel_l2(got, ref) <= FP32X2_TOL
 
 
+def test_initial_state_fp32fx2_matches_oracle(sfm, initial):
+    p, rs, dt, n, w, ref = initial
+    got = _run(sfm, rs, dt, n, w, sfm.SFM_FP32FX2)
+    assert pipeline.rel_l2(got, ref) <= FP32X2_TOL
+
+
 def test_initial_state_fp32f_matches_oracle(sfm, initial):
     p, rs, dt, n, w, ref = initial
     got = _run(sfm, rs, dt, n, w, sfm.SFM_FP32F)

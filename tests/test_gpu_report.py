@@ -122,7 +122,7 @@ def test_energy_matches_the_oracle_and_is_conserved(sfm, free):
     np.testing.assert_allclose(e1, A.energy(Ua, Ua - Da, dt), rtol=ENERGY_TOL)
 
 
-@pytest.mark.parametrize("prec", ["SFM_FP32F", "SFM_TF32X3"])
+@pytest.mark.parametrize("prec", ["SFM_FP32F", "SFM_TF32X3", "SFM_FP32FX2"])
 def test_fp32_class_energy_stays_near_fp64(sfm, free, prec):
     """FP32 state and sums: the energy carries the state's FP32 rounding."""
     p, rs, dt, n, w = free
@@ -141,7 +141,7 @@ def test_fp32_class_energy_stays_near_fp64(sfm, free, prec):
     np.testing.assert_allclose(got["energy_end"], got["energy_start"], rtol=1e-4)
 
 
-@pytest.mark.parametrize("prec", ["SFM_FP64", "SFM_FP32F", "SFM_TF32X3"])
+@pytest.mark.parametrize("prec", ["SFM_FP64", "SFM_FP32F", "SFM_TF32X3", "SFM_FP32FX2"])
 def test_sentinel_stops_an_unstable_run_early(sfm, free, prec):
     """Twice the CFL step: the state runs away within tens of steps; the
     sentinel must end a 50000-step run long before its end."""

@@ -31,6 +31,10 @@ FP32X2_TOL = 1e-5
 # emulation of a 64-subdomain k = 16 crop of the 192^3 model gave 8e-5 after
 # 4000 steps); held to the throughput metric's gate.
 FP32F_GATE = 1e-3
+# The same FP32 factors with a two-float state, two-float vectors and
+# compensated sums: the factors' rounding is the only FP32 rounding left (the
+# crop emulation: 5.2e-6 after 4000 steps); held to the FP32 target.
+FP32FX2_TOL = 1e-5
 
 
 @pytest.fixture(scope="module")
@@ -99,6 +103,15 @@ def test_uneven_fp32f_matches_oracle(sfm, uneven):
     assert pipeline.rel_l2(got, ref) <= FP32F_GATE
 
 
+def test_uneven_fp32fx2_matches_oracle(sfm, uneven):
+    p, rs, dt, n, w, ref = uneven
+    got = _run(sfm, rs, dt, n, w, sfm.SFM_FP32FX2)
+    f32f = _run(sfm, rs, dt, n, w, sfm.SFM_FP32F)
+    print(f"uneven FP32FX2 {pipeline.rel_l2(got, ref):.3e}, FP32F {pipeline.rel_l2(f32f, ref):.3e}")
+    assert pipeline.rel_l2(got, ref) <= FP32FX2_TOL
+    assert np.abs(got - ref).max() <= 10 * FP32FX2_TOL * np.abs(ref).max()
+
+
 def test_runs_are_bitwise_deterministic(sfm, uneven):
     p, rs, dt, n, w, ref = uneven
     a = _run(sfm, rs, dt, n, w, sfm.SFM_FP32)
@@ -124,7 +137,7 @@ def test_device_pointer_path_matches_host_path(sfm, uneven):
         sfm.sfm_destroy(h)
 
 
-@pytest.mark.parametrize("precision", [0, 2, 3])
+@pytest.mark.parametrize("precision", [0, 2, 3, 7])
 def test_block_shapes_give_identical_traces(sfm, uneven, precision):
     """Consumer warps and ring stages change the grid, the per-block pieces
     (units cut at different levels) and which warp runs a tile row, never the
@@ -142,7 +155,7 @@ def test_block_shapes_give_identical_traces(sfm, uneven, precision):
             assert np.array_equal(got, base), (ncw, nst)
         ncw, nst, us = sfm.sfm_autotune(h, precision, 50)
         assert ncw in (2, 4, 6, 8) and nst in (2, 3, 4, 6, 8, 12, 16) and us > 0
-        if precision == sfm.SFM_FP32F:
+        if precision in (sfm.SFM_FP32F, sfm.SFM_FP32FX2):
             assert nst % ncw == 0
         got, _ = sfm.sfm_run(h, precision, dt, n, w, rs.nshots, rs.nrec)
         assert np.array_equal(got, base)
@@ -302,6 +315,12 @@ def test_config1_fp32f_matches_oracle(sfm, cfg1):
     assert pipeline.rel_l2(got, ref) <= FP32F_GATE
 
 
+def test_config1_fp32fx2_matches_oracle(sfm, cfg1):
+    p, rs, dt, w, ref = cfg1
+    got = _run(sfm, rs, dt, p.nsteps, w, sfm.SFM_FP32FX2)
+    assert pipeline.rel_l2(got, ref) <= FP32FX2_TOL
+
+
 def per_trace_errors(got, ref):
     """Error of every (shot, receiver) trace relative to the RMS trace norm
     of its shot (rounding errors scale with the state, not with one trace's
@@ -388,3 +407,13 @@ def test_config2_geometry_fp32f_matches_oracle(sfm, cfg2_layered):
     assert pipeline.rel_l2(got, ref) <= FP32F_GATE
     assert per_trace_errors(got, ref).max() <= FP32F_GATE
 
+
+def test_config2_geometry_fp32fx2_matches_oracle(sfm, cfg2_layered):
+    """FP32 factor bytes at the FP32 target: every trace of the 4000-step
+    run within 1e-5 of the oracle."""
+    p, rs, dt, w, ref = cfg2_layered
+    got = _run(sfm, rs, dt, p.nsteps, w, sfm.SFM_FP32FX2)
+    print(f"config-2 geometry FP32FX2: {pipeline.rel_l2(got, ref):.3e}, "
+          f"worst trace {per_trace_errors(got, ref).max():.3e}")
+    assert pipeline.rel_l2(got, ref) <= FP32FX2_TOL
+    assert per_trace_errors(got, ref).max() <= FP32FX2_TOL
