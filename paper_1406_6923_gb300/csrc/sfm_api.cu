@@ -618,7 +618,8 @@ static int step_setup(sfm_handle* h, int nunits, const long long* src_off,
                       sfm::StepParams<typename P::S>& p, int* grid_out) {
     sfm_ext* x = ext(h);
     const int id = prec_id(P{});
-    const int ncw = x->ncw[id];
+    // a policy's kernel may take fewer consumer warps than asked for
+    const int ncw = std::min(x->ncw[id], sfm::step_max_ncw<P>());
     int nstage = x->nstage[id];
     // factored blocks are owned by warp (block index mod ncw) through fixed
     // stages: the ring depth must be a multiple of the warp count
@@ -1300,6 +1301,7 @@ static int autotune_impl(sfm_handle* h, int nsteps, int* ncw_out, int* nstage_ou
     double best = 1e300;
     int bn = ncw0, bs = nst0;
     for (int nc : kNcw) {
+        if (nc > sfm::step_max_ncw<P>()) continue;       // beyond the kernel's launch bounds
         for (int ns : kStage) {
             if (P::factored && ns % nc != 0) continue;   // see step_setup
             int gmax = 0;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
+#include <type_traits>
 #include <string>
 #include <vector>
 
@@ -65,6 +66,16 @@ struct StepParams {
     int* ustep;                  // instability sentinel: first step whose face update
                                  // was non-finite or beyond 1e30 (atomicMin), or NULL
 };
+
+// Launch bounds per policy.  The factored FP32 kernel is held to at most
+// four consumer warps so that four blocks fit on an SM (96 registers a
+// thread); the other policies take up to eight.
+template <class P>
+constexpr int step_max_ncw() { return std::is_same<P, PolF32F>::value ? 4 : 8; }
+template <class P>
+constexpr int step_max_threads() { return (step_max_ncw<P>() + 1) * 32; }
+template <class P>
+constexpr int step_min_blocks() { return std::is_same<P, PolF32F>::value ? 4 : 1; }
 
 constexpr int PANEL_NCW_MAX = 8;   // 16-shot groups (consumer warps) per panel block
 

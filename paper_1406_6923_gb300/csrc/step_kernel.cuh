@@ -5,6 +5,7 @@
 #include "sfm_internal.h"
 
 #include <cstdint>
+#include <type_traits>
 
 namespace sfm {
 
@@ -475,7 +476,7 @@ __device__ __forceinline__ int piece_blocks(int j0, int j1) {
 }
 
 template <class P>
-__global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typename P::S> p) {
+__global__ void __launch_bounds__(step_max_threads<P>(), step_min_blocks<P>()) step_kernel(StepParams<typename P::S> p) {
     using S = typename P::S;
     using C = typename P::C;
     using K = typename P::K;
@@ -570,9 +571,11 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
     unsigned cph = 0;
     bool dead = false;
     // factored path: issue the copies of piece pcx into staging set `set`
-    // (one cp.async group per call; zero padding written directly)
+    // (one cp.async group per call; zero padding written directly).  With
+    // skip0 the level-0 rows of U are left to the caller (phase B computes
+    // them in this block and writes them into the set itself).
     constexpr int EPV = (int)(16 / sizeof(S));   // state elements per 16-byte copy
-    auto stage = [&](int pcx, int set, const S* Ubuf) {
+    auto stage = [&](int pcx, int set, const S* Ubuf, bool skip0) {
         const int4 a0 = prec(pcx, 0), a1 = prec(pcx, 1);
         const int xj0 = a0.z, xj1 = a0.w, xb = a1.x & 255, xk = a1.x >> 8;
         const int xbp = ((xb + 7) >> 3) * 8;
@@ -587,8 +590,11 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
             for (int lj = warp; lj <= xnl; lj += ncw) {
                 const int j = xjl + lj;
                 for (int i = EPV * lane; i < xbp; i += 32 * EPV) {
-                    if (j < xk && i < xb) cp_async<16>(xU + lj * xbp + i, Ubuf + xso + j * xb + i);
-                    else *reinterpret_cast<float4*>(xU + lj * xbp + i) = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (j < xk && i < xb) {
+                        if (!(skip0 && j == 0)) cp_async<16>(xU + lj * xbp + i, Ubuf + xso + j * xb + i);
+                    } else {
+                        *reinterpret_cast<float4*>(xU + lj * xbp + i) = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
                 }
             }
             for (int lj = xja - xjl + warp; lj < xnl; lj += ncw) {
@@ -609,8 +615,11 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
         for (int lj = warp; lj <= xnl; lj += ncw) {
             const int j = xjl + lj;
             for (int i = lane; i < xbp; i += 32) {
-                if (j < xk && i < xb) cp_async<sizeof(S)>(xU + lj * xbp + i, Ubuf + xso + j * xb + i);
-                else xU[lj * xbp + i] = P::zero();
+                if (j < xk && i < xb) {
+                    if (!(skip0 && j == 0)) cp_async<sizeof(S)>(xU + lj * xbp + i, Ubuf + xso + j * xb + i);
+                } else {
+                    xU[lj * xbp + i] = P::zero();
+                }
             }
         }
         for (int lj = xja - xjl + warp; lj < xnl; lj += ncw) {
@@ -627,7 +636,7 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
         }
         cp_async_commit();
     };
-    bool pre = false;   // the first piece of this step was staged at the end of the last one
+    bool pre = false;   // the first piece of this step was staged during the last step's phase B
     for (int n = 0; n < p.nsteps; ++n) {
         const S* Ucur = p.U[n & 3];
         S* Unxt = p.U[(n + 1) & 3];
@@ -651,8 +660,8 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
             if constexpr (P::factored) {
                 const int set = (pc - pc0) & 1;
                 cbar(nct);
-                if (pc == pc0 && !pre) stage(pc, set, Ucur);
-                if (pc + 1 < pc1) stage(pc + 1, set ^ 1, Ucur);
+                if (pc == pc0 && !pre) stage(pc, set, Ucur, false);
+                if (pc + 1 < pc1) stage(pc + 1, set ^ 1, Ucur, false);
                 if (pc + 1 < pc1) {
                     cp_async_wait<1>();
                 } else {
@@ -828,7 +837,24 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
         if (!grid_wait(p.bar, (unsigned)(n + 1) * gridDim.x, p.err, p.timeout_ns, nct))
             return;
 
+        // Factored path: stage the first piece of step n+1 now, while phase
+        // B runs.  Every level of U^{n+1} it reads other than level 0 was
+        // written in phase A, before the barrier (a unit is never cut at
+        // level 1, so only a level-0 piece reads level 0, and its face
+        // update is done by this block below, which also writes those rows
+        // into the staging set).
+        pre = false;
+        if constexpr (P::factored) {
+            if (n + 1 < p.nsteps && pc0 < pc1) {
+                stage(pc0, 0, Unxt, prec(pc0, 0).z == 0);
+                pre = true;
+            }
+        }
+
         // ---------------- phase B: faces, Eq. (18) ----------------
+        // scratch for the face rows' increments and state (a staging set the
+        // next piece copies into only after the next phase A barrier)
+        C* const sB = sU + (NSET - 1) * SU;
         for (int pc = pc0; pc < pc1; ++pc) {
             const int4 r0 = prec(pc, 0);
             if (r0.z != 0) continue;                     // faces belong to the level-0 piece
@@ -837,11 +863,15 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
             const long long so = q * p.state_stride + r1.y;
             const S* mailq = mail + q * p.mail_stride;
             const int4* fr = p.frow + r1.w;
+            const bool to_stage = pre && pc == pc0;
             cbar(nct);
-            // sum of both sides' face data, lower subdomain index first
+            // sum of both sides' face data, lower subdomain index first; the
+            // face rows' increment and state are loaded in the same pass
             for (int t = threadIdx.x; t < b; t += nct) {
                 const int4 e = fr[t];
                 C v = P::ld(mailq + r1.w + t);
+                sB[t] = P::ld(p.dU + so + t);
+                sB[bpm + t] = P::ld(Ucur + so + t);
                 if (e.x >= 0) {
                     const C o = P::ld(mailq + e.x);
                     v = (e.z >> 16) ? P::add(o, v) : P::add(v, o);
@@ -857,27 +887,17 @@ __global__ void __launch_bounds__(STEP_BLOCK_MAX) step_kernel(StepParams<typenam
                 const C* v = sPhi + e.w;
                 typename P::Acc acc = P::acc0();
                 for (int c = 0; c < m; ++c) P::fma(acc, P::ld(H + c * m), v[c]);
-                const C d = P::add(P::ld(p.dU + so + t), P::mul(dt2, P::get(acc)));
+                const C d = P::add(sB[t], P::mul(dt2, P::get(acc)));
                 P::st(p.dU + so + t, d);
-                const C un = P::add(P::ld(Ucur + so + t), d);
+                const C un = P::add(sB[bpm + t], d);
                 P::st(Unxt + so + t, un);
+                if (to_stage) sU[t] = un;                // level 0 of staging set 0
                 if (!P::sane(un)) {
                     // unstable (time step above the CFL limit): every block
                     // leaves at the next device-wide barrier
                     if (p.ustep) atomicMin(p.ustep, n);
                     atomicCAS(p.err, 0, (int)SFM_ERR_UNSTABLE);
                 }
-            }
-        }
-        pre = false;
-        if constexpr (P::factored) {
-            // stage the first piece of step n+1 now: U^{n+1} is complete for
-            // every piece of this block (interior levels before the barrier,
-            // this block's face levels just above)
-            if (n + 1 < p.nsteps && pc0 < pc1) {
-                cbar(nct);
-                stage(pc0, 0, Unxt);
-                pre = true;
             }
         }
     }
