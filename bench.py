@@ -51,16 +51,17 @@ def parse():
     ap.add_argument("--impl", default="sfm", choices=["sfm", "reference"])
     ap.add_argument("--nsteps", type=int, default=None, help="time steps per run (default: 4000)")
     ap.add_argument("--precision", default="auto",
-                    choices=["auto", "fp32f", "tf32x3", "tf32", "fp32", "fp32fx2", "fp32x2", "fp64"])
+                    choices=["auto", "fp32f", "tf32x3", "tf32", "fp32", "fp32fx2", "fp32x2p", "fp32x2", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched config-3 object of the headline line")
     ap.add_argument("--cpu-sample-steps", type=int, default=600)
-    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "paper", "surrogate"],
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "paper", "paper10", "surrogate"],
                     help="cfg2: 192^3 cells, 512 subdomains, 1 shot (the headline); "
                          "cfg3: 256x256x128 cells, uneven subdomains, 64 shots; "
                          "paper: the 7x7x3 unit-cube layout of the paper's experiment at "
-                         "m = 10, k = 4, t in [0, 12.5]; surrogate: the learned surrogate "
+                         "its own m = 25 (b = 150), k = 3, t in [0, 12.5]; paper10: the same "
+                         "layout at m = 10, k = 4; surrogate: the learned surrogate "
                          "trained and judged on 24^3 blocks (m = 8, k = 16)")
     ap.add_argument("--sur-train", type=int, default=2000, help="surrogate workload: training blocks")
     ap.add_argument("--sur-test", type=int, default=200, help="surrogate workload: held-out blocks")
@@ -152,6 +153,26 @@ def peaks():
             return json.load(f), "measured"
     except OSError:
         return {"hbm_gbs": FALLBACK_HBM}, "fallback"
+
+
+def l2_read_gbs(torch, mbytes=32, repeats=64, iters=20):
+    """Read bandwidth of a 32 MB buffer that stays in the 129 MB L2: one
+    reduction kernel reads it ``repeats`` times (a view whose rows all alias
+    the buffer), after a warm-up, bytes read over CUDA-event time.  The roof
+    for a kernel that streams a working set held in L2."""
+    n = mbytes * 1024 * 1024 // 4
+    a = torch.ones(n, dtype=torch.float32, device="cuda")
+    v = a.as_strided((repeats, n), (0, 1))
+    for _ in range(3):
+        v.sum()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(iters):
+        v.sum()
+    e1.record()
+    torch.cuda.synchronize()
+    return float(n) * 4 * repeats * iters / (e0.elapsed_time(e1) * 1e-3) / 1e9
 
 
 def max_over_ranks(x, dist, device):
@@ -267,12 +288,16 @@ def reference_arm(args, rank, world):
 
 # ---------------------------------------------------------------------------
 
-MODES = ("fp32f", "tf32x3", "tf32", "fp32", "fp32fx2", "fp32x2")
+MODES = ("fp32f", "tf32x3", "tf32", "fp32", "fp32fx2", "fp32x2p", "fp32x2")
 DTYPE = {"fp32f": "f32", "tf32x3": "tf32x3", "tf32": "tf32", "fp32": "f32", "fp32fx2": "f32x2",
-         "fp32x2": "f32x2", "fp64": "f64"}
+         "fp32x2p": "f32x2", "fp32x2": "f32x2", "fp64": "f64"}
 # bytes per number: (S-fraction blocks or their factors, everything else)
 WORD = {"fp32f": (4, 4), "tf32x3": (4, 4), "tf32": (4, 4), "fp32": (4, 4), "fp32fx2": (4, 8),
-        "fp32x2": (8, 8), "fp64": (8, 8)}
+        "fp32x2p": (8, 8), "fp32x2": (8, 8), "fp64": (8, 8)}
+KERNEL = {"tf32x3": "panel_kernel", "tf32": "panel_kernel", "fp32x2p": "panel2_kernel"}
+# FP32 operations of one compensated two-float term g x in the two-float
+# panel products (two-product 2, two-sum 6, error sums 2, cross terms 2)
+X2_TERM_OPS = 12
 
 
 def build_workload(sfm, h, p, workload):
@@ -310,7 +335,8 @@ def measure_workload(sfm, torch, h, p, args, dt, nsteps, stream, local, dist, wo
     wav = torch.tensor(inputs.wavelet_samples(p, dt, nsteps), dtype=torch.float64, device="cuda")
     tr = torch.empty((nshots, nrec, nsteps + 1), dtype=torch.float64, device="cuda")
     modes = {"fp32f": sfm.SFM_FP32F, "tf32x3": sfm.SFM_TF32X3, "tf32": sfm.SFM_TF32,
-             "fp32": sfm.SFM_FP32, "fp32fx2": sfm.SFM_FP32FX2, "fp32x2": sfm.SFM_FP32X2,
+             "fp32": sfm.SFM_FP32, "fp32fx2": sfm.SFM_FP32FX2, "fp32x2p": sfm.SFM_FP32X2P,
+             "fp32x2": sfm.SFM_FP32X2,
              "fp64": sfm.SFM_FP64}
 
     def run(prec):
@@ -333,7 +359,7 @@ def measure_workload(sfm, torch, h, p, args, dt, nsteps, stream, local, dist, wo
     if force:
         chosen = force
     else:
-        chosen = next(n for n in ("fp32f", "tf32x3", "fp32", "fp32fx2", "fp32x2", "fp64")
+        chosen = next(n for n in ("fp32f", "tf32x3", "fp32", "fp32fx2", "fp32x2p", "fp32x2", "fp64")
                       if errors.get(n) is not None and errors[n] <= GATE)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
     timed = {}
@@ -385,15 +411,38 @@ def measure_workload(sfm, torch, h, p, args, dt, nsteps, stream, local, dist, wo
     return chosen, errors, timed, statistics.mean(e2e_t), host_w.nbytes, host_tr.nbytes
 
 
+def alu_peak(clock_mhz):
+    """FP32 operations per second of the whole GPU: 152 SMs x 128 FP32 lanes
+    x the SM clock (an FMA counts as one operation)."""
+    return 152 * 128 * clock_mhz * 1e6
+
+
 def roofline_of(p, name, t, nsteps, pk, pk_kind, traffic):
     word = WORD[name]
     bytes_step = algorithmic_bytes_per_step(p, p.nshots, receiver_row_numbers(p), word)
     achieved = bytes_step * nsteps / (t["kernel_ms"] * 1e-3) / 1e9
-    return {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
-            "peak_source": f"{pk_kind} HBM copy",
-            "kernel": "panel_kernel" if name in ("tf32x3", "tf32") else "step_kernel",
-            "kernel_ms": t["kernel_ms"], "bytes_per_time_step": bytes_step}
+    out = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+           "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
+           "peak_source": f"{pk_kind} HBM copy",
+           "kernel": KERNEL.get(name, "step_kernel"),
+           "kernel_ms": t["kernel_ms"], "bytes_per_time_step": bytes_step}
+    if name == "fp32x2p":
+        # compensated CUDA-core products: bound by FP32 issue, not by bytes
+        b = face_modes(p).sum(axis=1)
+        k = np.asarray(p.k_sub)
+        terms = float(((2 * k - 1) * b * b).sum()) * p.nshots
+        ops = terms * X2_TERM_OPS * nsteps
+        clk = (t.get("clocks") or {}).get("sm_mhz") or 2070.0
+        peak = alu_peak(clk) / 1e12
+        ach = ops / (t["kernel_ms"] * 1e-3) / 1e12
+        out = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+               "frac": ach / peak, "traffic": traffic,
+               "peak_source": f"152 SMs x 128 FP32 lanes x {clk:.0f} MHz (FP32 operations, FMA = 1)",
+               "kernel": "panel2_kernel", "kernel_ms": t["kernel_ms"],
+               "two_float_terms_per_time_step": terms, "fp32_ops_per_term": X2_TERM_OPS,
+               "hbm": {"achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                       "frac": achieved / pk["hbm_gbs"], "bytes_per_time_step": bytes_step}}
+    return out
 
 
 def cpu_baseline_run(threads, sample_steps):
@@ -434,7 +483,8 @@ def main():
         surrogate_experiment(sfm, torch, args)
         return
     makers = {"cfg2": inputs.config2, "cfg3": inputs.config3,
-              "paper": lambda: inputs.paper_layout(m=10, k=4)}   # the widest blocks the stepping takes
+              "paper": lambda: inputs.paper_layout(m=25, k=3),       # the paper's m and n, b = 150
+              "paper10": lambda: inputs.paper_layout(m=10, k=4)}
     p = makers[args.workload]()
     stream = torch.cuda.current_stream()
     h = sfm.sfm_create(local)
@@ -460,6 +510,14 @@ def main():
     pk, pk_kind = peaks()
     traffic = read_traffic() if (args.workload == "cfg2" and chosen == "fp32f") else None
     roof = roofline_of(p, chosen, t, nsteps, pk, pk_kind, traffic)
+    if roof["bound"] == "hbm":
+        # the factored FP32 coefficient set of config 2 stays in L2 after the
+        # first time step: its own roof, measured here
+        l2 = l2_read_gbs(torch)
+        roof["l2"] = {"achieved": roof["achieved"], "peak": l2, "unit": "GB/s",
+                      "frac": roof["achieved"] / l2,
+                      "peak_source": "measured here: one reduction kernel reading a 32 MB buffer held "
+                                     "in L2 64 times, bytes read over CUDA-event time"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "cfg2":
@@ -521,7 +579,7 @@ def batched_extra(sfm, torch, args, local, pk, pk_kind):
     sfm.sfm_set_stream(h, stream.cuda_stream)
     dt, nsteps, dtf, rep, depth_cut, build_s = build_workload(sfm, h, p, "cfg3")
     chosen, errors, timed, e2e_s, h2d, d2h = measure_workload(
-        sfm, torch, h, p, args, dt, nsteps, stream, local, None, 1, 3, 2, 1, also=("tf32x3",))
+        sfm, torch, h, p, args, dt, nsteps, stream, local, None, 1, 3, 2, 1, also=("tf32x3", "fp32x2"))
     sfm.sfm_destroy(h)
     ncell = p.nx * p.ny * p.nz
     rate = lambda ms: ncell * nsteps * (dt / dtf) * p.nshots / (ms * 1e-3)
@@ -533,6 +591,14 @@ def batched_extra(sfm, torch, args, local, pk, pk_kind):
            "block_shape": t["block_shape"], "clocks": t["clocks"],
            "e2e": {"value": ncell * nsteps * (dt / dtf) * p.nshots / e2e_s, "unit": UNIT,
                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}}
+    if "fp32x2" in timed and chosen != "fp32x2":
+        # the single-shot two-float kernel on the same workload (every shot
+        # its own unit, every block read once per shot)
+        tq = timed["fp32x2"]
+        res["fp32x2_single_shot_kernel"] = {
+            "value": rate(tq["ms"]), "ms_per_step": tq["ms"], "trace_err_vs_fp64": errors.get("fp32x2"),
+            "roofline": roofline_of(p, "fp32x2", tq, nsteps, pk, pk_kind, None),
+            "block_shape": tq["block_shape"], "clocks": tq["clocks"]}
     if "tf32x3" in timed and chosen != "tf32x3":
         tp = timed["tf32x3"]
         err = errors.get("tf32x3")

@@ -69,11 +69,18 @@ enum sfm_precision {
                                 (11 significant bits; deep ROMs diverge)       */
     SFM_BF16 = 6,            /* not built: sfm_run returns SFM_ERR_ARG (BF16's
                                 8-bit significand is coarser than TF32's)      */
-    SFM_FP32FX2 = 7          /* SFM_FP32F's FP32 Cholesky factors (the same
+    SFM_FP32FX2 = 7,         /* SFM_FP32F's FP32 Cholesky factors (the same
                                 coefficient bytes) with the state, the vectors
                                 of each product and its sums in SFM_FP32X2's
                                 two-float form: the factors' rounding is the
                                 only FP32 rounding                             */
+    SFM_FP32X2P = 8          /* multi-shot panels as SFM_TF32X3 (shots 16 at a
+                                time, each S-fraction block read once for the
+                                16), with SFM_FP32X2's two-float blocks, state
+                                and face data and compensated products on the
+                                CUDA cores: SFM_FP32X2's accuracy for deep
+                                ROMs that no FP32-coefficient mode steps
+                                within 1e-3                                    */
 };
 
 /* flags for sfm_run */
@@ -122,7 +129,11 @@ int sfm_set_stream(sfm_handle* h, void* stream);
  *                 (homogeneous Neumann); must be symmetric: if nbr[s][f] = t
  *                 then nbr[t][f^1] = s.
  * Limits of the stepping kernels: m <= 32 on a face, block width
- * b_s = sum of the six face counts in 1..64, k_s * b_s <= 16384.
+ * b_s = sum of the six face counts in 1..192, k_s * b_s <= 16384.  Blocks
+ * wider than 64 (the paper's 5 x 5 modes per face give b = 150) step in
+ * SFM_FP64, SFM_FP32X2 and SFM_FP32 and build with sfm_build_roms; the
+ * factored and panel modes, the energy report (SFM_ENERGY), sfm_cut_depth,
+ * the surrogate calls and sfm_run_static return SFM_ERR_ARG for them.
  * Resets coefficients, sources and receivers.
  * Errors: SFM_ERR_ARG for inconsistent topology or sizes beyond the limits.
  */
@@ -188,10 +199,10 @@ int sfm_set_initial(sfm_handle* h, int nshots, int npairs, const int* pair_shot,
  * f_q(t_n)) are evaluated at t_n = n*dt and
  *     delta^{n+1} = delta^n + dt^2 a^n,  U^{n+1} = U^n + delta^{n+1}.
  *   precision      SFM_FP64, SFM_FP32, SFM_FP32X2, SFM_FP32F or SFM_FP32FX2
- *                  (one kernel over every shot), SFM_TF32X3 or SFM_TF32 (the
- *                  multi-shot panels); the factored modes first factor every
- *                  block used (SFM_ERR_NOT_SPD if one is not positive
- *                  definite in FP64)
+ *                  (one kernel over every shot), SFM_TF32X3, SFM_TF32 or
+ *                  SFM_FP32X2P (the multi-shot panels); the factored
+ *                  modes first factor every block used (SFM_ERR_NOT_SPD if
+ *                  one is not positive definite in FP64)
  *   wavelet        [nshots][nsteps] FP64 samples f_q(t_n)
  *   traces         [nshots][nrec][nsteps+1] FP64 output, d_r(t_n), n=0..nsteps
  *   flags          SFM_DEVICE_PTR: wavelet and traces are device pointers

@@ -150,6 +150,10 @@ int set_topology_internal(sfm_handle* h, int nsub, const int* k_sub, const int* 
 int set_coeffs_device(sfm_handle* h, const double* d_coeffs);
 }  // namespace sfm
 
+// Largest dynamic shared memory the builder's one-block-per-matrix kernels
+// take; wider blocks work in global memory.
+constexpr size_t kBuilderSmem = 200 * 1024;
+
 // Orthonormalise a batch of N x n blocks in place by Cholesky QR done twice:
 // X = Q R with R = R2 R1.  Rout (S x n x n) receives R when not NULL.
 static int cholqr2(sfm_handle* h, const Gemm& gemm, double* X, long long sX, int N, int n, int S,
@@ -157,16 +161,23 @@ static int cholqr2(sfm_handle* h, const Gemm& gemm, double* X, long long sX, int
                    double* Rout, int* d_err, double* d_ratio, double* min_ratio) {
     cudaStream_t st = h->stream;
     const long long nn = (long long)n * n;
-    const size_t smem = 2 * nn * sizeof(double);
-    if (smem > 200 * 1024) return bfail(h, SFM_ERR_ARG, "builder: block width too large");
-    BCK(h, cudaFuncSetAttribute(sfm::bld::chol_rinv_kernel,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // work space of the factorisation: shared memory, or global for wide blocks
+    size_t smem = 2 * nn * sizeof(double);
+    double* ws = nullptr;
+    DevGuard guard_ws(ws);
+    if (smem > kBuilderSmem) {
+        BCK(h, dmalloc(ws, (size_t)S * 2 * nn));
+        smem = 0;
+    } else {
+        BCK(h, cudaFuncSetAttribute(sfm::bld::chol_rinv_kernel,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
     for (int pass = 0; pass < 2; ++pass) {
         double* R = pass ? R2 : R1;
         double* Ri = pass ? R2i : R1i;
         BLK(h, gemm(true, false, n, n, N, 1.0, X, N, sX, X, N, sX, 0.0, Gm, n, nn, S));
         sfm::bld::chol_rinv_kernel<<<S, 128, smem, st>>>(Gm, R, Ri, n, d_err,
-                                                          pass == 0 ? d_ratio : nullptr);
+                                                          pass == 0 ? d_ratio : nullptr, ws);
         BCK(h, cudaGetLastError());
         BLK(h, gemm(false, false, N, n, n, 1.0, X, N, sX, Ri, n, nn, 0.0, tmp, N, (long long)N * n, S));
         BCK(h, cudaMemcpy2DAsync(X, sX * sizeof(double), tmp, (size_t)N * n * sizeof(double),
@@ -311,7 +322,8 @@ static int build_impl(sfm_handle* h, const int* m_sub, const int* k_sub, double 
             if (c.mf[f] > (ncell[u] - 1) * (ncell[v] - 1))
                 return bfail(h, SFM_ERR_ARG, "sfm_build_roms: more modes than open-face nodes");
         }
-        if (c.b > 64) return bfail(h, SFM_ERR_ARG, "sfm_build_roms: block width b > 64");
+        if (c.b > sfm::BMAX_WIDE)
+            return bfail(h, SFM_ERR_ARG, "sfm_build_roms: block width b above " + std::to_string(sfm::BMAX_WIDE));
     }
     int rc = sfm::set_topology_internal(h, nsub, k_sub, mface.data(), nbr.data());
     if (rc != SFM_OK) return rc;
@@ -526,10 +538,17 @@ static int build_impl(sfm_handle* h, const int* m_sub, const int* k_sub, double 
         BCK(h, dmalloc(Gam, (size_t)S * k * bb));
         BCK(h, dmalloc(Gh, (size_t)S * k * bb));
         BCK(h, dmalloc(c.Ginv, (size_t)S * k * bb));
-        const size_t gsm = 5 * bb * sizeof(double);
-        BCK(h, cudaFuncSetAttribute(sfm::bld::gamma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)gsm));
-        sfm::bld::gamma_kernel<<<S, 256, gsm, st>>>(al, Cm, Rl, b, k, Gam, Gh, c.Ginv, d_err);
+        size_t gsm = 5 * bb * sizeof(double);
+        double* gws = nullptr;
+        DevGuard guard_gws(gws);
+        if (gsm > kBuilderSmem) {
+            BCK(h, dmalloc(gws, (size_t)S * 5 * bb));   // wide blocks: global work space
+            gsm = 0;
+        } else {
+            BCK(h, cudaFuncSetAttribute(sfm::bld::gamma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)gsm));
+        }
+        sfm::bld::gamma_kernel<<<S, 256, gsm, st>>>(al, Cm, Rl, b, k, Gam, Gh, c.Ginv, d_err, gws);
         BCK(h, cudaGetLastError());
         // scatter into the stepping layout: per subdomain Gamma_1..k then Gammahat_1..k
         for (int i = 0; i < S; ++i) {
@@ -562,10 +581,17 @@ static int build_impl(sfm_handle* h, const int* m_sub, const int* k_sub, double 
         BCK(h, cudaMemsetAsync(d_nreg, 0, sizeof(int), st));
         BCK(h, cudaFuncSetAttribute(sfm::psd_project_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)sfm::PSD_SMEM));
-        for (int s0 = 0; s0 < h->nsub; s0 += 65535) {
-            const int ns = std::min(65535, h->nsub - s0);
-            sfm::psd_project_kernel<<<dim3(2 * h->kmax, ns), 256, sfm::PSD_SMEM, st>>>(
-                d_coef, h->d_coef_off + s0, h->d_b + s0, h->d_k + s0, d_nreg);
+        // blocks wider than 64: a global work space per launch block
+        double* pws = nullptr;
+        DevGuard guard_pws(pws);
+        const size_t per_sub = (size_t)2 * h->kmax * 2 * h->bmax * (h->bmax + 1);   // doubles
+        const int pchunk = (int)std::max<size_t>(1, std::min<size_t>(65535, (64u << 20) / per_sub));
+        if (h->bmax > 64) BCK(h, dmalloc(pws, per_sub * pchunk));
+        const int sstep = h->bmax > 64 ? pchunk : 65535;
+        for (int s0 = 0; s0 < h->nsub; s0 += sstep) {
+            const int ns = std::min(sstep, h->nsub - s0);
+            sfm::psd_project_kernel<<<dim3(2 * h->kmax, ns), 256, h->bmax > 64 ? 0 : sfm::PSD_SMEM, st>>>(
+                d_coef, h->d_coef_off + s0, h->d_b + s0, h->d_k + s0, d_nreg, pws, h->bmax);
         }
         BCK(h, cudaGetLastError());
         BCK(h, cudaMemcpyAsync(&nreg, d_nreg, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -955,7 +981,7 @@ extern "C" int sfm_build_roms_surrogate(sfm_handle* h, sfm_net* net, const int* 
         const size_t csm = 2 * bb * sizeof(double);
         BCK(h, cudaFuncSetAttribute(sfm::bld::chol_rinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)csm));
-        sfm::bld::chol_rinv_kernel<<<S, 128, csm, st>>>(Gh1, R0, R0i, b, d_e, d_err2);
+        sfm::bld::chol_rinv_kernel<<<S, 128, csm, st>>>(Gh1, R0, R0i, b, d_e, d_err2, nullptr);
         BCK(h, cudaGetLastError());
         BLK(h, gemm(false, true, b, b, b, 1.0, R0i, b, bb, R0i, b, bb, 0.0, Gi, b, bb, S));   // (F^T F)^{-1}
         BCK(h, dmalloc(LF, (size_t)S * sF));

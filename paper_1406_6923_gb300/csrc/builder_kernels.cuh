@@ -259,10 +259,13 @@ __global__ void cg_dir_kernel(double* P, const double* Z, int N, double* rz, con
 // Small dense factorisations, one block per matrix (column-major, ld = n).
 //
 // chol_rinv: A = R^T R (R upper), writes R and R^{-1}; ratio[s] = min diag(R)
-// / max diag(R); err on a non-positive pivot.
+// / max diag(R); err on a non-positive pivot.  The work space (2 n*n) is the
+// block's dynamic shared memory, or, for blocks too wide for it, its slice
+// of the global array ws.
 __global__ void chol_rinv_kernel(const double* A, double* Rout, double* Rinv, int n, int* err,
-                                 double* ratio) {
-    extern __shared__ double sm[];
+                                 double* ratio, double* ws) {
+    extern __shared__ double sm_dyn[];
+    double* sm = ws ? ws + (long long)blockIdx.x * 2 * n * n : sm_dyn;
     double* a = sm;            // n*n, column-major: a[i + n*j]
     double* ri = sm + n * n;   // n*n
     const long long s = blockIdx.x;
@@ -385,12 +388,14 @@ __device__ bool sm_inverse(double* A, double* W, int n, int* piv) {
 // alpha: k blocks, C: k-1 blocks (block (j+1, j) of T_L), R1: b x b; all
 // column-major b x b.  Outputs Gamma, Gammahat (k blocks each, symmetrised)
 // and Ginv (k blocks: G_j^{-1}).  err = SFM_ERR_NOT_SPD when a diagonal of
-// Gamma_j, j < k, is not positive (a cheap necessary check).
+// Gamma_j, j < k, is not positive (a cheap necessary check).  Work space 5 b*b:
+// dynamic shared memory, or the block's slice of ws for wide blocks.
 __global__ void gamma_kernel(const double* alpha, const double* C, const double* R1, int b, int k,
-                             double* Gam, double* Gh, double* Ginv, int* err) {
+                             double* Gam, double* Gh, double* Ginv, int* err, double* ws) {
     // alpha: [S][k] blocks; C: level-major [k-1][S] blocks; R1: [S]
-    extern __shared__ double sm[];
+    extern __shared__ double sm_dyn[];
     const int bb = b * b;
+    double* sm = ws ? ws + (long long)blockIdx.x * 5 * bb : sm_dyn;
     double* G = sm;
     double* Gi = sm + bb;
     double* prev = sm + 2 * bb;
@@ -511,14 +516,18 @@ __global__ void finish_project_kernel(const double* Z, const double* Ginv, int b
 // a cyclic Jacobi eigen-decomposition; such blocks are counted.  A shift
 // would be wrong here: it gives a singular inverse-mass direction a finite
 // mass, and with the large stiffness paired with it a spurious fast mode.
-constexpr int REG_LD = 65;
-constexpr size_t PSD_SMEM = 2 * 64 * REG_LD * sizeof(double);
+// Blocks up to 64 wide work in shared memory (A and V, 64 rows of 65);
+// wider ones in the block's slice of the global work space ws (2 b(b+1)
+// numbers a block, rows of b + 1).
+constexpr int PSD_NARROW_LD = 65;
+constexpr size_t PSD_SMEM = 2 * 64 * PSD_NARROW_LD * sizeof(double);
 __global__ void __launch_bounds__(256) psd_project_kernel(double* coef, const long long* coef_off,
                                                           const int* sub_b, const int* sub_k,
-                                                          int* nproj) {
-    extern __shared__ double psd_smem[];      // A and V, 64 x REG_LD each
-    double* A = psd_smem;
-    double* V = psd_smem + 64 * REG_LD;
+                                                          int* nproj, double* ws, int bmax) {
+    extern __shared__ double psd_smem[];
+    const int REG_LD = ws ? bmax + 1 : PSD_NARROW_LD;
+    double* A = ws ? ws + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * 2LL * bmax * REG_LD : psd_smem;
+    double* V = A + (ws ? bmax : 64) * REG_LD;
     __shared__ double s_cs[2];
     __shared__ int s_ok;
     const int s = blockIdx.y, blk = blockIdx.x;

@@ -146,6 +146,10 @@ int sfm_cut_depth(sfm_handle* h, double tau, int* depth_out, int depth_cap, int*
         h->err = "sfm_cut_depth: no coefficients";
         return SFM_ERR_STATE;
     }
+    if (h->bmax > sfm::BMAX_NARROW) {
+        h->err = "sfm_cut_depth: blocks wider than 64 (its eigenvalue ranges work in 64-wide shared memory)";
+        return SFM_ERR_ARG;
+    }
     if (depth_out && depth_cap < h->nsub) {
         h->err = "sfm_cut_depth: depth_out holds fewer than nsub entries";
         return SFM_ERR_ARG;

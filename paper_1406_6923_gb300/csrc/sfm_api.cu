@@ -93,12 +93,18 @@ void set_global_error(const std::string& msg) { g_err = msg; }
 struct PanelCache {
     float *coef = nullptr, *H = nullptr, *src = nullptr, *rrows = nullptr;
     long long *d_coef_off = nullptr, *d_src_off = nullptr;
+    // two-float mode: padded two-float tiles of the symmetric blocks, their
+    // per-subdomain offsets (floats) and H_f as (hi, lo) pairs, built on
+    // first use
+    float *coef2 = nullptr, *H2 = nullptr, *rrows2 = nullptr;
+    long long* d_coef2_off = nullptr;
     int *d_sub_rp_ptr = nullptr, *d_sub_rp = nullptr;
     int ngroups = 0, rpmax = 0;
     bool valid = false;
     void release() {
         dfree(coef); dfree(H); dfree(src); dfree(rrows);
         dfree(d_coef_off); dfree(d_src_off); dfree(d_sub_rp_ptr); dfree(d_sub_rp);
+        dfree(coef2); dfree(H2); dfree(rrows2); dfree(d_coef2_off);
         ngroups = rpmax = 0;
         valid = false;
     }
@@ -121,9 +127,10 @@ struct sfm_ext {
     int* d_ustep = nullptr;            // instability sentinel step (INT_MAX: none)
     PanelCache pc;
     PanelBufs pb;
-    // panel block shape per mode (index 0: 1xTF32, 1: 3xTF32): consumer warps
-    // (16-shot groups per task) and ring stages; sfm_autotune overwrites them
-    int pncw[2] = {4, 4}, pnstage[2] = {4, 4};
+    // panel block shape per mode (index 0: 1xTF32, 1: 3xTF32, 2: two-float):
+    // consumer warps (16-shot groups per task) and ring stages; sfm_autotune
+    // overwrites them
+    int pncw[3] = {4, 4, 4}, pnstage[3] = {4, 4, 2};
     int* d_task_ptr = nullptr;
     int4* d_task = nullptr;
     int task_grid = -1, task_ncw = -1, task_ngroups = -1;
@@ -267,7 +274,8 @@ int sfm_set_topology(sfm_handle* h, int nsub, const int* k_sub, const int* m_fac
         if (b == 0) return fail(h, SFM_ERR_ARG, "sfm_set_topology: subdomain with b = 0");
         if ((long long)b * k_sub[s] > 256 * 64)
             return fail(h, SFM_ERR_ARG, "sfm_set_topology: k*b too large");
-        if (b > 64) return fail(h, SFM_ERR_ARG, "sfm_set_topology: block width b > 64");
+        if (b > sfm::BMAX_WIDE)
+            return fail(h, SFM_ERR_ARG, "sfm_set_topology: block width b above " + std::to_string(sfm::BMAX_WIDE));
     }
     h->nsub = nsub;
     h->k.assign(k_sub, k_sub + nsub);
@@ -513,13 +521,13 @@ int sfm_debug_set(sfm_handle* h, int key, long long value) {
     if (key == 3) {
         if (value < 1 || value > 8) return fail(h, SFM_ERR_ARG, "sfm_debug_set: consumer warps 1..8");
         for (int i = 0; i < 8; ++i) ext(h)->ncw[i] = (int)value;
-        for (int i = 0; i < 2; ++i) ext(h)->pncw[i] = (int)value;
+        for (int i = 0; i < 3; ++i) ext(h)->pncw[i] = (int)value;
         return SFM_OK;
     }
     if (key == 4) {
         if (value < 2 || value > 16) return fail(h, SFM_ERR_ARG, "sfm_debug_set: ring stages 2..16");
         for (int i = 0; i < 8; ++i) ext(h)->nstage[i] = (int)value;
-        for (int i = 0; i < 2; ++i) ext(h)->pnstage[i] = (int)value;
+        for (int i = 0; i < 3; ++i) ext(h)->pnstage[i] = (int)value;
         return SFM_OK;
     }
     return fail(h, SFM_ERR_ARG, "sfm_debug_set: unknown key");
@@ -624,6 +632,15 @@ static int step_setup(sfm_handle* h, int nunits, const long long* src_off,
     // factored blocks are owned by warp (block index mod ncw) through fixed
     // stages: the ring depth must be a multiple of the warp count
     if (P::factored) nstage = (nstage + ncw - 1) / ncw * ncw;
+    // wide blocks: fewer ring stages when the requested ring does not fit
+    {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        const int step = P::factored ? ncw : 1;
+        while (nstage - step >= 2 && sfm::step_smem_bytes<P>(h->kmax, h->bmax, nstage) > (size_t)optin)
+            nstage -= step;
+    }
     int gmax = 0;
     if (sfm::step_max_grid<P>(ncw, sfm::step_smem_bytes<P>(h->kmax, h->bmax, nstage), &gmax) != 0)
         return fail(h, SFM_ERR_ARG, "stepping: subdomain blocks too large for shared memory");
@@ -780,14 +797,26 @@ static int energy_of(sfm_handle* h, const T* U, const T* D, int nshots, double d
     }
 }
 
-static int energy_of_panel(sfm_handle* h, const float* U, const float* D, int nshots, double dt,
+// panel state (FP32 panels, or two-float panels in mode 2) -> FP64 state layout
+static cudaError_t from_panel_any(int mode, const float* in, double* out, int nshots, long long n,
+                                  cudaStream_t st) {
+    return mode == 2 ? sfm::launch_from_panel2(in, out, nshots, n, st)
+                     : sfm::launch_from_panel(in, out, nshots, n, st);
+}
+
+static cudaError_t to_panel_any(int mode, const double* in, float* out, int nshots, long long n,
+                                cudaStream_t st) {
+    return mode == 2 ? sfm::launch_to_panel2(in, out, nshots, n, st) : sfm::launch_to_panel(in, out, nshots, n, st);
+}
+
+static int energy_of_panel(sfm_handle* h, int mode, const float* U, const float* D, int nshots, double dt,
                            double* out) {
     const size_t n = (size_t)nshots * h->nstate;
     double *U64 = nullptr, *D64 = nullptr;
     cudaError_t e = dalloc(U64, n);
     if (e == cudaSuccess) e = dalloc(D64, n);
-    if (e == cudaSuccess) e = sfm::launch_from_panel(U, U64, nshots, h->nstate, h->stream);
-    if (e == cudaSuccess) e = sfm::launch_from_panel(D, D64, nshots, h->nstate, h->stream);
+    if (e == cudaSuccess) e = from_panel_any(mode, U, U64, nshots, h->nstate, h->stream);
+    if (e == cudaSuccess) e = from_panel_any(mode, D, D64, nshots, h->nstate, h->stream);
     int rc = e == cudaSuccess ? energy_f64(h, U64, D64, nshots, dt, out) : cuda_fail(h, e, "energy");
     dfree(U64);
     dfree(D64);
@@ -807,6 +836,9 @@ static int run_impl(sfm_handle* h, double dt, int nsteps, const double* wavelet,
                     int flags, double* kernel_ms) {
     using T = typename P::S;
     sfm_ext* x = ext(h);
+    if (P::factored && h->bmax > sfm::BMAX_NARROW)
+        return fail(h, SFM_ERR_ARG, "factored modes: blocks wider than 64 (a factor product is one "
+                                    "warp's registers); use SFM_FP64, SFM_FP32X2 or SFM_FP32");
     int rc = prepare<P>(h);
     if (rc != SFM_OK) return rc;
     auto& c = cache_of(h, P{});
@@ -958,21 +990,29 @@ static int run_impl(sfm_handle* h, double dt, int nsteps, const double* wavelet,
 }
 
 // ---------------------------------------------------------------------------
-// Multi-shot panel modes (SFM_TF32X3, SFM_TF32): shots stepped 16 at a time
-// with tensor-core factor products (panel.cu).
+// Multi-shot panel modes (SFM_TF32X3, SFM_TF32, SFM_FP32X2P): shots stepped
+// 16 at a time with tensor-core factor products or two-float CUDA-core
+// products (panel.cu).
 
-static int panel_mode_of(int precision) { return precision == SFM_TF32X3 ? 3 : 1; }
-static int panel_slot(int mode) { return mode == 3 ? 1 : 0; }
+static bool is_panel(int precision) {
+    return precision == SFM_TF32X3 || precision == SFM_TF32 || precision == SFM_FP32X2P;
+}
+static int panel_mode_of(int precision) {
+    return precision == SFM_TF32X3 ? 3 : precision == SFM_FP32X2P ? 2 : 1;
+}
+static int panel_slot(int mode) { return mode == 3 ? 1 : mode == 2 ? 2 : 0; }
 
 // FP32 data of the panel path, built once per set of coefficients, sources
 // and receivers: the FP32 Cholesky factors (factored in FP64) in 72-float
 // padded tiles, H_f and the receiver rows in FP32, the source rows of every
 // (shot, subdomain) pair in the panel of its (group, subdomain) unit.
-static int prepare_panel(sfm_handle* h) {
+static int prepare_panel2(sfm_handle* h);
+
+static int prepare_panel(sfm_handle* h, int mode) {
     sfm_ext* x = ext(h);
     PanelCache& c = x->pc;
     const int ngroups = (h->nshots + 15) / 16;
-    if (c.valid && c.ngroups == ngroups) return SFM_OK;
+    if (c.valid && c.ngroups == ngroups) return mode == 2 ? prepare_panel2(h) : SFM_OK;
     c.release();
     cudaStream_t st = h->stream;
     const long long ntiles = h->ntcoef / 64;
@@ -1044,6 +1084,35 @@ static int prepare_panel(sfm_handle* h) {
     c.ngroups = ngroups;
     c.rpmax = rpmax;
     c.valid = true;
+    return mode == 2 ? prepare_panel2(h) : SFM_OK;
+}
+
+// Two-float data of SFM_FP32X2P (once per set of coefficients): the
+// symmetric blocks in padded two-float tiles, H_f and the receiver rows as
+// (hi, lo) pairs.
+static int prepare_panel2(sfm_handle* h) {
+    PanelCache& c = ext(h)->pc;
+    if (c.coef2) return SFM_OK;
+    cudaStream_t st = h->stream;
+    const long long ntiles = h->ntcoef / 64;
+    std::vector<long long> coff(h->nsub);
+    for (int s = 0; s < h->nsub; ++s) coff[s] = h->tcoef_off[s] / 64 * 144;
+    cudaError_t e = dalloc(c.coef2, (size_t)ntiles * 144);
+    if (e == cudaSuccess) e = sfm::launch_pack_sym2(h->d_coef64, h->d_coef_off, h->d_tcoef_off, h->d_b, h->d_k,
+                                                    h->nsub, c.coef2, st);
+    if (e == cudaSuccess) e = upload(c.d_coef2_off, coff.data(), coff.size(), st);
+    if (e == cudaSuccess) e = dalloc(c.H2, 2 * (size_t)h->nH);
+    if (e == cudaSuccess)
+        e = sfm::launch_convert<sfm::PolF32x2>(h->d_H64, reinterpret_cast<float2*>(c.H2), (size_t)h->nH, st);
+    if (e == cudaSuccess) e = dalloc(c.rrows2, 2 * (size_t)std::max<long long>(h->nrrow, 1));
+    if (e == cudaSuccess && h->nrrow > 0)
+        e = sfm::launch_convert<sfm::PolF32x2>(h->d_rrows64, reinterpret_cast<float2*>(c.rrows2),
+                                               (size_t)h->nrrow, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        dfree(c.coef2); dfree(c.H2); dfree(c.rrows2); dfree(c.d_coef2_off);
+        return cuda_fail(h, e, "two-float panel data");
+    }
     return SFM_OK;
 }
 
@@ -1052,9 +1121,9 @@ static int panel_setup(sfm_handle* h, int mode, int* grid_out, int* ncw_out, int
     sfm_ext* x = ext(h);
     const int slot = panel_slot(mode);
     const int ngroups = x->pc.ngroups;
-    const int ncw = std::max(1, std::min(x->pncw[slot], std::min(ngroups, sfm::PANEL_NCW_MAX)));
+    const int ncw = std::max(1, std::min(x->pncw[slot], std::min(ngroups, sfm::panel_max_ncw(mode))));
     const int nstage = x->pnstage[slot];
-    const size_t smem = sfm::panel_smem_bytes(ncw, nstage, h->bmax, x->pc.rpmax);
+    const size_t smem = sfm::panel_smem_bytes(mode, ncw, nstage, h->bmax, x->pc.rpmax);
     int gmax = 0;
     if (sfm::panel_max_grid(mode, ncw, smem, &gmax) != 0)
         return fail(h, SFM_ERR_ARG, "panel modes: blocks too large for shared memory");
@@ -1082,16 +1151,19 @@ static int panel_setup(sfm_handle* h, int mode, int* grid_out, int* ncw_out, int
 static int run_panel_impl(sfm_handle* h, int mode, double dt, int nsteps, const double* wavelet,
                           double* traces, int flags, double* kernel_ms, bool zero_source = false) {
     sfm_ext* x = ext(h);
-    int rc = prepare_panel(h);
+    if (h->bmax > sfm::BMAX_NARROW)
+        return fail(h, SFM_ERR_ARG, "panel modes: blocks wider than 64 (eight 8-row tiles a warp)");
+    int rc = prepare_panel(h, mode);
     if (rc != SFM_OK) return rc;
     PanelCache& c = x->pc;
     PanelBufs& r = x->pb;
     cudaStream_t st = h->stream;
     const int ngroups = c.ngroups;
-    const size_t nst = (size_t)ngroups * h->nstate * 16;
-    const size_t nml = (size_t)ngroups * h->nmail * 16;
+    const size_t words = mode == 2 ? 2 : 1;            // floats per number
+    const size_t nst = (size_t)ngroups * h->nstate * 16 * words;
+    const size_t nml = (size_t)ngroups * h->nmail * 16 * words;
     const size_t nwav = (size_t)ngroups * 16 * nsteps;
-    const size_t npart = (size_t)ngroups * (nsteps + 1) * std::max(h->nrpairs, 1) * 16;
+    const size_t npart = (size_t)ngroups * (nsteps + 1) * std::max(h->nrpairs, 1) * 16 * words;
     const size_t ntr = (size_t)h->nshots * h->nrec * (nsteps + 1);
     { size_t hs = r.n_state; CK(h, grow(r.U, hs, nst)); }
     { size_t hs = r.n_state; CK(h, grow(r.dU, hs, nst)); r.n_state = hs; }
@@ -1129,8 +1201,8 @@ static int run_panel_impl(sfm_handle* h, int mode, double dt, int nsteps, const 
             return fail(h, SFM_ERR_STATE, "sfm_run: initial state set for a different shot count");
         if (h->init_delta) {
             // restored U^0 and delta^0
-            CK(h, sfm::launch_to_panel(h->d_init_U64, r.U, h->nshots, h->nstate, st));
-            CK(h, sfm::launch_to_panel(h->d_init_V64, r.dU, h->nshots, h->nstate, st));
+            CK(h, to_panel_any(mode, h->d_init_U64, r.U, h->nshots, h->nstate, st));
+            CK(h, to_panel_any(mode, h->d_init_V64, r.dU, h->nshots, h->nstate, st));
             launches += 2;
         } else {
             // delta^0 = dt V^0 - dt^2/2 a_hom(U^0), in FP64 (Algorithm 1 step 1.4)
@@ -1143,8 +1215,8 @@ static int run_panel_impl(sfm_handle* h, int mode, double dt, int nsteps, const 
             cudaError_t e1 = cudaSuccess;
             if (rc == SFM_OK) {
                 if ((e1 = sfm::launch_start_delta(h->d_init_V64, A, dt, n64, D, st)) == cudaSuccess &&
-                    (e1 = sfm::launch_to_panel(h->d_init_U64, r.U, h->nshots, h->nstate, st)) == cudaSuccess &&
-                    (e1 = sfm::launch_to_panel(D, r.dU, h->nshots, h->nstate, st)) == cudaSuccess)
+                    (e1 = to_panel_any(mode, h->d_init_U64, r.U, h->nshots, h->nstate, st)) == cudaSuccess &&
+                    (e1 = to_panel_any(mode, D, r.dU, h->nshots, h->nstate, st)) == cudaSuccess)
                     e1 = cudaStreamSynchronize(st);
                 launches += 3;
             }
@@ -1156,7 +1228,7 @@ static int run_panel_impl(sfm_handle* h, int mode, double dt, int nsteps, const 
     }
     if (flags & SFM_ENERGY) {
         x->energy.assign(2 * (size_t)h->nshots, 0.0);
-        rc = energy_of_panel(h, r.U, r.dU, h->nshots, dt, x->energy.data());
+        rc = energy_of_panel(h, mode, r.U, r.dU, h->nshots, dt, x->energy.data());
         if (rc != SFM_OK) return rc;
     }
     rc = ensure_ustep(h);
@@ -1172,13 +1244,17 @@ static int run_panel_impl(sfm_handle* h, int mode, double dt, int nsteps, const 
     p.ncw = ncw; p.nstage = nstage; p.bmax = h->bmax; p.rpmax = c.rpmax;
     p.nstate = h->nstate; p.nmail = h->nmail;
     p.task_ptr = x->d_task_ptr; p.task = x->d_task;
-    p.coef_off = c.d_coef_off; p.coef = c.coef;
-    p.state_off = h->d_state_off; p.mail_off = h->d_mail_off; p.frow = h->d_frow; p.H = c.H;
+    p.coef_off = mode == 2 ? c.d_coef2_off : c.d_coef_off;
+    p.coef = mode == 2 ? c.coef2 : c.coef;
+    p.state_off = h->d_state_off; p.mail_off = h->d_mail_off; p.frow = h->d_frow;
+    p.H = mode == 2 ? c.H2 : c.H;
     p.src_off = c.d_src_off; p.src = c.src; p.wavelet = r.wav;
-    p.sub_rp_ptr = c.d_sub_rp_ptr; p.sub_rp = c.d_sub_rp; p.rp_off = h->d_rp_off; p.rrows = c.rrows;
+    p.sub_rp_ptr = c.d_sub_rp_ptr; p.sub_rp = c.d_sub_rp; p.rp_off = h->d_rp_off;
+    p.rrows = mode == 2 ? c.rrows2 : c.rrows;
     p.nrpairs = h->nrpairs; p.partial = r.partial;
     p.U = r.U; p.dU = r.dU; p.mail0 = r.mail[0]; p.mail1 = r.mail[1];
     p.dt2 = (float)(dt * dt);
+    p.dt2lo = (float)(dt * dt - (double)p.dt2);
     p.bar = h->d_bar; p.err = h->d_err; p.timeout_ns = x->timeout_ns; p.skip_arrive = x->skip_arrive;
     p.ustep = x->d_ustep;
     CK(h, cudaEventRecord(x->ev0, st));
@@ -1187,8 +1263,12 @@ static int run_panel_impl(sfm_handle* h, int mode, double dt, int nsteps, const 
     ++launches;
     CK(h, cudaEventRecord(x->ev1, st));
     if (h->nrpairs > 0) {
-        CK(h, sfm::launch_panel_traces(r.partial, h->d_rec_ptr, h->d_rec_pairs, h->nshots, nsteps,
-                                       h->nrec, h->nrpairs, d_traces, x->d_bad, st));
+        if (mode == 2)
+            CK(h, sfm::launch_panel_traces2(r.partial, h->d_rec_ptr, h->d_rec_pairs, h->nshots, nsteps,
+                                            h->nrec, h->nrpairs, d_traces, x->d_bad, st));
+        else
+            CK(h, sfm::launch_panel_traces(r.partial, h->d_rec_ptr, h->d_rec_pairs, h->nshots, nsteps,
+                                           h->nrec, h->nrpairs, d_traces, x->d_bad, st));
     } else {
         CK(h, cudaMemsetAsync(d_traces, 0, ntr * sizeof(double), st));
     }
@@ -1217,7 +1297,7 @@ static int run_panel_impl(sfm_handle* h, int mode, double dt, int nsteps, const 
     if (herr != 0) return fail(h, herr, "device error during stepping");
     if (bad) return fail(h, SFM_ERR_UNSTABLE, "non-finite traces (time step above the CFL limit?)");
     if ((flags & SFM_ENERGY) && !zero_source) {
-        rc = energy_of_panel(h, r.U, r.dU, h->nshots, dt, x->energy.data() + h->nshots);
+        rc = energy_of_panel(h, mode, r.U, r.dU, h->nshots, dt, x->energy.data() + h->nshots);
         if (rc != SFM_OK) return rc;
     }
     return SFM_OK;
@@ -1230,6 +1310,8 @@ extern "C" int sfm_run(sfm_handle* h, int precision, double dt, int nsteps, cons
         return fail(h, SFM_ERR_STATE, "sfm_run: coefficients, sources and receivers must be set");
     if (nsteps < 1 || !(dt > 0.0) || !wavelet || !traces)
         return fail(h, SFM_ERR_ARG, "sfm_run: bad arguments");
+    if ((flags & SFM_ENERGY) && h->bmax > sfm::BMAX_NARROW)
+        return fail(h, SFM_ERR_ARG, "sfm_run: the energy report takes blocks up to 64 wide");
     CK(h, cudaSetDevice(h->device));
     sfm_ext* x = ext(h);
     x->ck_prec = -1;
@@ -1250,7 +1332,7 @@ extern "C" int sfm_run(sfm_handle* h, int precision, double dt, int nsteps, cons
         rc = run_impl<sfm::PolF32F>(h, dt, nsteps, wavelet, traces, flags, kernel_ms);
     else if (precision == SFM_FP32FX2)
         rc = run_impl<sfm::PolF32Fx2>(h, dt, nsteps, wavelet, traces, flags, kernel_ms);
-    else if (precision == SFM_TF32X3 || precision == SFM_TF32)
+    else if (is_panel(precision))
         rc = run_panel_impl(h, panel_mode_of(precision), dt, nsteps, wavelet, traces, flags, kernel_ms);
     else if (precision == SFM_BF16)
         return fail(h, SFM_ERR_ARG, "sfm_run: BF16 products are not built (an 8-bit significand "
@@ -1334,7 +1416,7 @@ static int autotune_panel(sfm_handle* h, int mode, int nsteps, int* ncw_out, int
     static const int kNcw[] = {1, 2, 4, 8};
     static const int kStage[] = {2, 3, 4, 6, 8};
     sfm_ext* x = ext(h);
-    int rc = prepare_panel(h);
+    int rc = prepare_panel(h, mode);
     if (rc != SFM_OK) return rc;
     const int slot = panel_slot(mode);
     const int ncw0 = x->pncw[slot], nst0 = x->pnstage[slot];
@@ -1343,9 +1425,10 @@ static int autotune_panel(sfm_handle* h, int mode, int nsteps, int* ncw_out, int
     int bn = ncw0, bs = nst0;
     for (int nc : kNcw) {
         if (nc > 1 && nc > x->pc.ngroups) continue;
+        if (nc > sfm::panel_max_ncw(mode)) continue;
         for (int ns : kStage) {
             int gmax = 0;
-            if (sfm::panel_max_grid(mode, nc, sfm::panel_smem_bytes(nc, ns, h->bmax, x->pc.rpmax), &gmax) != 0 ||
+            if (sfm::panel_max_grid(mode, nc, sfm::panel_smem_bytes(mode, nc, ns, h->bmax, x->pc.rpmax), &gmax) != 0 ||
                 gmax < 1)
                 continue;
             x->pncw[slot] = nc;
@@ -1388,7 +1471,7 @@ extern "C" int sfm_autotune(sfm_handle* h, int precision, int nsteps, int* ncw, 
         rc = autotune_impl<sfm::PolF32F>(h, nsteps, ncw, nstage, us_per_step);
     else if (precision == SFM_FP32FX2)
         rc = autotune_impl<sfm::PolF32Fx2>(h, nsteps, ncw, nstage, us_per_step);
-    else if (precision == SFM_TF32X3 || precision == SFM_TF32)
+    else if (is_panel(precision))
         rc = autotune_panel(h, panel_mode_of(precision), nsteps, ncw, nstage, us_per_step);
     else
         rc = fail(h, SFM_ERR_ARG, "sfm_autotune: unknown precision");
@@ -1465,13 +1548,14 @@ extern "C" int sfm_checkpoint(sfm_handle* h, void* buf, size_t* bytes) {
     double* dU = U + n;
     const int slot = x->ck_steps % 4;                   // U^n lives in buffer n mod 4
     cudaError_t e;
-    if (x->ck_prec == SFM_TF32X3 || x->ck_prec == SFM_TF32) {
+    if (is_panel(x->ck_prec)) {
         // panel state (updated in place) back to the state layout
+        const int mode = panel_mode_of(x->ck_prec);
         double *dUx = nullptr, *dDx = nullptr;
         e = dalloc(dUx, n);
         if (e == cudaSuccess) e = dalloc(dDx, n);
-        if (e == cudaSuccess) e = sfm::launch_from_panel(x->pb.U, dUx, x->ck_nshots, h->nstate, h->stream);
-        if (e == cudaSuccess) e = sfm::launch_from_panel(x->pb.dU, dDx, x->ck_nshots, h->nstate, h->stream);
+        if (e == cudaSuccess) e = from_panel_any(mode, x->pb.U, dUx, x->ck_nshots, h->nstate, h->stream);
+        if (e == cudaSuccess) e = from_panel_any(mode, x->pb.dU, dDx, x->ck_nshots, h->nstate, h->stream);
         if (e == cudaSuccess) e = fetch_state(dUx, dDx, n, h->stream, U, dU);
         dfree(dUx);
         dfree(dDx);

@@ -77,7 +77,20 @@ constexpr int step_max_threads() { return (step_max_ncw<P>() + 1) * 32; }
 template <class P>
 constexpr int step_min_blocks() { return std::is_same<P, PolF32F>::value ? 4 : 1; }
 
+// Block widths b = sum of a subdomain's six face counts.  The FP64, FP32 and
+// two-float stepping, the offline builder and the projections take b up to
+// BMAX_WIDE (the paper's m = 25 per face gives b = 150); the factored modes,
+// the multi-shot panels, the energy report, the usable-depth cut, the
+// surrogate and the allocation-free entry point keep each block's 8x8 tiles
+// in one warp's registers or a 64-wide shared-memory array and take b up to
+// BMAX_NARROW.
+constexpr int BMAX_NARROW = 64;
+constexpr int BMAX_WIDE = 192;
+
 constexpr int PANEL_NCW_MAX = 8;   // 16-shot groups (consumer warps) per panel block
+// the two-float panel kernel (mode 2) takes at most four consumer warps
+// (255 registers a thread, one block of five warps per SM)
+inline int panel_max_ncw(int mode) { return mode == 2 ? 4 : PANEL_NCW_MAX; }
 
 // Device-side description of a multi-shot panel run (panel.cu): shots in
 // groups of 16, every array FP32.  Offsets are in numbers.
@@ -108,6 +121,7 @@ struct PanelParams {
     float* mail0;
     float* mail1;
     float dt2;
+    float dt2lo;                 // two-float mode: dt^2 - dt2 (rounded)
     unsigned int* bar;
     int* err;
     unsigned long long timeout_ns;
@@ -115,8 +129,9 @@ struct PanelParams {
     int* ustep;                  // instability sentinel (as StepParams::ustep)
 };
 
-// panel launchers (panel.cu); mode 1 = 1xTF32, 3 = 3xTF32 products
-size_t panel_smem_bytes(int ncw, int nstage, int bmax, int rpmax);
+// panel launchers (panel.cu); mode 1 = 1xTF32, 3 = 3xTF32 products (FP32
+// panels), 2 = two-float panels with compensated CUDA-core products
+size_t panel_smem_bytes(int mode, int ncw, int nstage, int bmax, int rpmax);
 int panel_max_grid(int mode, int ncw, size_t smem, int* grid_out);
 cudaError_t launch_panel(int mode, const PanelParams& p, int grid, cudaStream_t st);
 // LPT assignment of the tasks (subdomain, group chunk of at most ncw groups)
@@ -129,6 +144,16 @@ cudaError_t launch_pad_tiles(const float* in, float* out, long long ntiles, cuda
 cudaError_t launch_to_panel(const double* in, float* out, int nshots, long long n, cudaStream_t st);
 // FP32 panels -> FP64 [nshots][n]
 cudaError_t launch_from_panel(const float* in, double* out, int nshots, long long n, cudaStream_t st);
+// traces from the two-float partial sums of mode 2
+cudaError_t launch_panel_traces2(const float* partial, const int* rec_ptr, const int* rec_pairs,
+                                 int nshots, int nsteps, int nrec, int nrpairs, double* traces,
+                                 int* bad, cudaStream_t st);
+// two-float mode: FP64 [nshots][n] <-> [ngroups][n][16][hi, lo] (natural shot order)
+cudaError_t launch_to_panel2(const double* in, float* out, int nshots, long long n, cudaStream_t st);
+cudaError_t launch_from_panel2(const float* in, double* out, int nshots, long long n, cudaStream_t st);
+// two-float padded tiles of every symmetric block (144 floats a tile)
+cudaError_t launch_pack_sym2(const double* master, const long long* master_off, const long long* tile_off,
+                             const int* sub_b, const int* sub_k, int nsub, float* out, cudaStream_t st);
 // source rows of (shot, subdomain) pairs into their unit's panels:
 // rows[off64[i] .. + len[i]) go to column dst[i] % 16 of out + dst[i] - dst[i] % 16
 cudaError_t launch_src_panels(const double* rows, const long long* off64, const long long* dst,

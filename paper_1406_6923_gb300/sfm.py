@@ -32,6 +32,7 @@ SFM_TF32X3 = 4
 SFM_TF32 = 5
 SFM_BF16 = 6
 SFM_FP32FX2 = 7
+SFM_FP32X2P = 8
 
 SFM_DEVICE_PTR = 1
 SFM_ENERGY = 2

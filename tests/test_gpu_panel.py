@@ -179,3 +179,68 @@ def test_panel_checkpoint_continues_bitwise(sfm, uneven20):
         sfm.sfm_destroy(h)
     np.testing.assert_array_equal(first, whole[:, :, :n1 + 1])
     np.testing.assert_array_equal(second, whole[:, :, n1:])
+
+
+# SFM_FP32X2P: the panels in two-float form (blocks, state, face data and
+# the compensated products of SFM_FP32X2), held to the FP32-class target.
+FP32X2_TOL = 1e-5
+
+
+def test_fp32x2p_uneven_ragged_group_matches_oracle(sfm, uneven20):
+    p, rs, dt, n, w, ref = uneven20
+    got = run(sfm, rs, sfm.SFM_FP32X2P, dt, n, w)
+    err = pipeline.rel_l2(got, ref)
+    per = per_trace_errors(got, ref)
+    print(f"FP32X2P uneven, 20 shots: rel L2 {err:.3e}, worst trace {per.max():.3e}")
+    assert err < FP32X2_TOL
+    assert per.max() < FP32X2_TOL
+
+
+def test_fp32x2p_64_shot_uneven_crop_matches_oracle(sfm, crop64):
+    p, rs, dt, n, w, ref = crop64
+    got = run(sfm, rs, sfm.SFM_FP32X2P, dt, n, w)
+    err = pipeline.rel_l2(got, ref)
+    per = per_trace_errors(got, ref)
+    print(f"FP32X2P 64-shot crop: rel L2 {err:.3e}, worst trace {per.max():.3e}")
+    assert err < FP32X2_TOL
+    assert per.max() < FP32X2_TOL
+
+
+def test_fp32x2p_agrees_with_the_single_shot_two_float_mode(sfm, crop64):
+    """The same two-float blocks and state as SFM_FP32X2, summed in another
+    order: the two differ by two-float rounding only."""
+    p, rs, dt, n, w, ref = crop64
+    a = run(sfm, rs, sfm.SFM_FP32X2P, dt, n, w)
+    b = run(sfm, rs, sfm.SFM_FP32X2, dt, n, w)
+    d = pipeline.rel_l2(a, b)
+    print(f"FP32X2P vs FP32X2: {d:.3e}; FP32X2 vs oracle {pipeline.rel_l2(b, ref):.3e}")
+    assert d < 0.1 * FP32X2_TOL
+
+
+def test_fp32x2p_traces_do_not_depend_on_the_block_shape(sfm, crop64):
+    p, rs, dt, n, w, ref = crop64
+    runs = [run(sfm, rs, sfm.SFM_FP32X2P, dt, n, w, shape=s) for s in ((1, 2), (2, 3), (4, 4), (4, 8))]
+    for r in runs[1:]:
+        np.testing.assert_array_equal(r, runs[0])
+
+
+def test_fp32x2p_checkpoint_continues(sfm, uneven20):
+    """The two-float panel state goes through the FP64 checkpoint (hi + lo
+    rounded to FP64 and split again): a restored run continues the N+M-step
+    traces to far below the mode's own error."""
+    p, rs, dt, n, w, ref = uneven20
+    n1 = n // 2
+    h = sfm.sfm_create(0)
+    try:
+        load_into(sfm, h, rs)
+        whole, _ = sfm.sfm_run(h, sfm.SFM_FP32X2P, dt, n, w, rs.nshots, rs.nrec)
+        first, _ = sfm.sfm_run(h, sfm.SFM_FP32X2P, dt, n1, np.ascontiguousarray(w[:, :n1]),
+                               rs.nshots, rs.nrec)
+        blob = sfm.sfm_checkpoint(h)
+        sfm.sfm_restore(h, blob)
+        second, _ = sfm.sfm_run(h, sfm.SFM_FP32X2P, dt, n - n1, np.ascontiguousarray(w[:, n1:]),
+                                rs.nshots, rs.nrec)
+    finally:
+        sfm.sfm_destroy(h)
+    np.testing.assert_array_equal(first, whole[:, :, :n1 + 1])
+    assert pipeline.rel_l2(second, whole[:, :, n1:]) < 1e-9
