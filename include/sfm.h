@@ -607,6 +607,19 @@ int sfm_last_launches(const sfm_handle* h, int* launches);
  */
 int sfm_debug_set(sfm_handle* h, int key, long long value);
 
+/*
+ * Read-bandwidth probe (no counterpart in the paper; the measured roof for a
+ * kernel whose working set stays in L2).  On `device`, allocates a buffer of
+ * `bytes` (rounded down to 16), zeroes it, reads it once to bring it into
+ * L2, then times one launch that reads it `repeats` times with 16-byte loads
+ * cached in L2 only (CUDA events); *gbs receives bytes * repeats / time in
+ * GB/s.  A buffer larger than L2 measures HBM instead.  The buffer is freed
+ * before return and the caller's current device is restored.
+ * Errors: SFM_ERR_ARG (bytes < 16, repeats < 1, NULL gbs), SFM_ERR_CUDA
+ * (device, allocation or launch; message in sfm_last_error(NULL)).
+ */
+int sfm_probe_read_gbs(int device, size_t bytes, int repeats, double* gbs);
+
 #ifdef __cplusplus
 }
 #endif

@@ -784,12 +784,20 @@ __device__ __forceinline__ void x2_merge(float& s, float& e, float s2, float e2)
 
 // Readout of level j of the state at U (global, the unit's panel) with the
 // two-float receiver rows: compensated sums over the lane's rows, merged
-// across the eight row lanes, added to acc[pair][pos(c)] as (hi, lo).
+// across the eight row lanes, added to acc[pair][pos(c)] as (hi, lo).  The
+// lane's state values are loaded once for all the unit's pairs.
 template <int NT>
 __device__ __forceinline__ void readout_level2(const PanelParams& p, const float* U, int b, int j, int rp0,
                                                int nrp, float* acc) {
     const int lane = threadIdx.x & 31, q = lane >> 3, a = lane & 7;
     const float* Uj = U + (long long)j * b * 32;
+    float4 u0[NT], u1[NT];
+#pragma unroll
+    for (int R = 0; R < NT; ++R) {
+        const int r = 8 * R + a;
+        u0[R] = u1[R] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < b) ldg2_row(Uj, r, q, u0[R], u1[R]);
+    }
     for (int e = 0; e < nrp; ++e) {
         const int pr = p.sub_rp[rp0 + e];
         const float* row = p.rrows + 2 * (p.rp_off[pr] + (long long)j * b);
@@ -798,13 +806,11 @@ __device__ __forceinline__ void readout_level2(const PanelParams& p, const float
         for (int R = 0; R < NT; ++R) {
             const int r = 8 * R + a;
             if (r < b) {
-                float4 u0, u1;
-                ldg2_row(Uj, r, q, u0, u1);
                 const float2 w = *reinterpret_cast<const float2*>(row + 2 * r);
-                x2_fma(ts[0], te[0], w.x, w.y, u0.x, u0.y);
-                x2_fma(ts[1], te[1], w.x, w.y, u0.z, u0.w);
-                x2_fma(ts[2], te[2], w.x, w.y, u1.x, u1.y);
-                x2_fma(ts[3], te[3], w.x, w.y, u1.z, u1.w);
+                x2_fma(ts[0], te[0], w.x, w.y, u0[R].x, u0[R].y);
+                x2_fma(ts[1], te[1], w.x, w.y, u0[R].z, u0[R].w);
+                x2_fma(ts[2], te[2], w.x, w.y, u1[R].x, u1[R].y);
+                x2_fma(ts[3], te[3], w.x, w.y, u1[R].z, u1[R].w);
             }
         }
 #pragma unroll
@@ -1189,9 +1195,12 @@ static int panel_max_grid_f(F kernel, int ncw, size_t smem, int* grid_out) {
     int per_sm = 0, nsm = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    // a shape that does not fit is "no grid"; its errors are cleared
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, (ncw + 1) * 32, smem) != cudaSuccess) {
+        cudaGetLastError();
         return -1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, (ncw + 1) * 32, smem);
+    }
     if (per_sm < 1) return -1;
     *grid_out = per_sm * nsm;
     return 0;

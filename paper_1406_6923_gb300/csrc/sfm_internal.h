@@ -75,7 +75,7 @@ constexpr int step_max_ncw() { return std::is_same<P, PolF32F>::value ? 4 : 8; }
 template <class P>
 constexpr int step_max_threads() { return (step_max_ncw<P>() + 1) * 32; }
 template <class P>
-constexpr int step_min_blocks() { return std::is_same<P, PolF32F>::value ? 4 : 1; }
+constexpr int step_min_blocks() { return std::is_same<P, PolF32F>::value ? 4 : 0; }   // 0: no minimum
 
 // Block widths b = sum of a subdomain's six face counts.  The FP64, FP32 and
 // two-float stepping, the offline builder and the projections take b up to

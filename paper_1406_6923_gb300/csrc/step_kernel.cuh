@@ -925,8 +925,15 @@ int step_max_grid(int ncw, size_t smem, int* grid_out) {
     int per_sm = 0, nsm = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(step_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<P>, (ncw + 1) * 32, smem);
+    // a shape whose shared memory does not fit is "no grid"; the failed
+    // calls' errors are cleared so that no later launch check reports them
+    if (cudaFuncSetAttribute(step_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<P>, (ncw + 1) * 32, smem) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
     if (per_sm < 1) return -1;
     *grid_out = per_sm * nsm;
     return 0;

@@ -46,7 +46,8 @@ EXPORTS = ["sfm_create", "sfm_destroy", "sfm_last_error", "sfm_set_stream", "sfm
            "sfm_cut_depth", "sfm_checkpoint", "sfm_restore", "sfm_run_report",
            "sfm_net_create", "sfm_net_destroy", "sfm_net_last_error", "sfm_net_params",
            "sfm_net_grad", "sfm_net_adam", "sfm_net_forward", "sfm_raw_encode",
-           "sfm_net_fit_decoder", "sfm_net_decode", "sfm_ntd_error", "sfm_build_roms_surrogate", "sfm_build_roms_shifts"]
+           "sfm_net_fit_decoder", "sfm_net_decode", "sfm_ntd_error", "sfm_build_roms_surrogate", "sfm_build_roms_shifts",
+           "sfm_probe_read_gbs"]
 
 
 class sfm_build_report(C.Structure):
@@ -134,6 +135,7 @@ def load(path=LIB_PATH):
         "sfm_build_roms_shifts": (_i, [_p, _ip, _ip, _dp, _i, C.c_double, C.POINTER(sfm_build_report)]),
         "sfm_build_roms_surrogate": (_i, [_p, _p, _ip, _ip, C.c_double, C.c_double, C.c_double, _ip,
                                           C.POINTER(sfm_surrogate_report), C.POINTER(sfm_build_report)]),
+        "sfm_probe_read_gbs": (_i, [_i, C.c_size_t, _i, _dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -304,6 +306,14 @@ def sfm_plan_pieces(nunits, k_sub, grid):
     _check(None, load().sfm_plan_pieces(int(nunits), len(k), kp, int(grid), ptr.ctypes.data_as(_ip),
                                         pieces.ctypes.data_as(_ip), n.value, C.byref(n)))
     return ptr, pieces
+
+
+def sfm_probe_read_gbs(device, nbytes, repeats):
+    """Read bandwidth (GB/s) of ``nbytes`` streamed ``repeats`` times in one
+    launch (L2-resident when ``nbytes`` fits in L2)."""
+    v = C.c_double()
+    _check(None, load().sfm_probe_read_gbs(int(device), int(nbytes), int(repeats), C.byref(v)))
+    return v.value
 
 
 def sfm_last_launches(h):
