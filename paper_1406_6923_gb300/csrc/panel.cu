@@ -301,12 +301,13 @@ constexpr int RHO_STAGE_MAX = 8;   // receiver pairs per subdomain staged with t
 
 // Floats of a warp's shared-memory region: the state slots, two levels of
 // staged receiver rows (when rpmax <= RHO_STAGE_MAX) and their offsets,
-// rounded up to 128 bytes so that every warp's region (and the 16-byte
-// copies into its slots) starts aligned.
+// phi_{j-1} in the accumulator layout (4 nt numbers a lane), rounded up to
+// 128 bytes so that every warp's region (and the 16-byte copies into its
+// slots) starts aligned.
 __host__ __device__ inline long long warp_region_floats(int bmax, int rpmax) {
     const long long bpad = ((bmax + 7) / 8) * 8;
     const long long rho = rpmax <= RHO_STAGE_MAX ? rpmax : 0;
-    const long long n = NSLOT * bpad * PROW + 2 * rho * bpad + 2 * rho;
+    const long long n = NSLOT * bpad * PROW + 2 * rho * bpad + 2 * rho + 16 * bpad;
     return (n + 31) / 32 * 32;
 }
 
@@ -406,7 +407,10 @@ __device__ __noinline__ void unit_a(const PanelParams& p, int s, int g, int b, i
     __syncwarp();
     issue(0);
     issue(1);
-    float phiprev[NT][4];
+    // phi_{j-1}, lane-private in shared memory (entry (i, e) of this lane at
+    // (i*4 + e)*32 + lane): a register copy would spill
+    const long long rho_n = p.rpmax <= RHO_STAGE_MAX ? p.rpmax : 0;
+    float* const phiprev = slots + NSLOT * ss + 2 * rho_n * bpad + 2 * rho_n;
     for (int j = 0; j < k; ++j) {
         cp_async_wait<1>();
         __syncwarp();
@@ -452,7 +456,7 @@ __device__ __noinline__ void unit_a(const PanelParams& p, int s, int g, int b, i
             for (int i = 0; i < NT; ++i)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    phiprev[i][e] = y[i][e];
+                    phiprev[(i * 4 + e) * 32 + lane] = y[i][e];
                     x[i][e] += y[i][e];
                 }
             st_panel<NT>(mail + ((long long)g * p.nmail + p.mail_off[s]) * 16, b, x);
@@ -462,8 +466,9 @@ __device__ __noinline__ void unit_a(const PanelParams& p, int s, int g, int b, i
             for (int i = 0; i < NT; ++i)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    x[i][e] = (y[i][e] - phiprev[i][e]) + x[i][e];
-                    phiprev[i][e] = y[i][e];
+                    float* pp = phiprev + (i * 4 + e) * 32 + lane;
+                    x[i][e] = (y[i][e] - *pp) + x[i][e];
+                    *pp = y[i][e];
                 }
             tl = ring_take(ring, stages, stage_elems, full, err, tmo);
             if (tl) factor_panel<NT, MODE>(tl, x, y);     // y = a_j
