@@ -53,6 +53,29 @@ def test_config2_bytes_per_step():
     assert bench.algorithmic_bytes_per_step(p, 1, rec, (4, 8)) == 2 * want - 4 * blocks
 
 
+def test_two_float_panel_roofline_counts_fp32_operations():
+    """The two-float panel mode is bound by FP32 issue: its roof counts
+    12 FP32 operations per compensated term and (2k - 1) b^2 terms per
+    subdomain, shot and time step, against 152 SMs x 128 lanes x the
+    clock; the HBM figure rides beside it."""
+    import bench
+    p = inputs.config3()
+    t = {"kernel_ms": 1000.0, "clocks": {"sm_mhz": 2000.0}}
+    r = bench.roofline_of(p, "fp32x2p", t, 100, {"hbm_gbs": 7000.0}, "measured", None)
+    b = bench.face_modes(p).sum(axis=1)
+    k = np.asarray(p.k_sub)
+    terms = float(((2 * k - 1) * b * b).sum()) * p.nshots
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["two_float_terms_per_time_step"] == terms
+    assert abs(r["peak"] - 152 * 128 * 2000e6 / 1e12) < 1e-9
+    assert abs(r["achieved"] - terms * 12 * 100 / 1.0 / 1e12) < 1e-6 * r["achieved"]
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+    assert r["hbm"]["bytes_per_time_step"] == bench.algorithmic_bytes_per_step(
+        p, p.nshots, bench.receiver_row_numbers(p), (8, 8))
+    # the other modes keep the HBM roof
+    assert bench.roofline_of(p, "tf32x3", t, 100, {"hbm_gbs": 7000.0}, "measured", None)["bound"] == "hbm"
+
+
 @pytest.mark.slow
 def test_reference_arm_prints_one_contract_line():
     """``bench.py --impl reference`` (the FP64 oracle on a bounded sample of
