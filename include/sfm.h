@@ -130,7 +130,7 @@ int sfm_set_stream(sfm_handle* h, void* stream);
  *                 then nbr[t][f^1] = s.
  * Limits of the stepping kernels: m <= 32 on a face, block width
  * b_s = sum of the six face counts in 1..192, k_s * b_s <= 16384.  Blocks
- * wider than 64 (the paper's 5 x 5 modes per face give b = 150) step in
+ * wider than 64 (the paper's 25 modes per face give b = 150) step in
  * SFM_FP64, SFM_FP32X2 and SFM_FP32 and build with sfm_build_roms; the
  * factored and panel modes, the energy report (SFM_ENERGY), sfm_cut_depth,
  * the surrogate calls and sfm_run_static return SFM_ERR_ARG for them.

@@ -401,7 +401,7 @@ def paper_layout(seed=SEED, cells_per_unit=20, m=25, k=3):
     """Stand-in for the paper's experiment (section "Numerical experiments"),
     in its dimensionless units: the box [0,7] x [0,7] x [0,3] split into
     7 x 7 x 3 unit cubes of ``cells_per_unit``^3 cells, m = 25 face modes
-    (5 x 5), k = n = 3 levels, c(x, y) from ``skew_fracture`` (its model is
+    (the 25 lowest p^2 + q^2 cosine modes), k = n = 3 levels, c(x, y) from ``skew_fracture`` (its model is
     shown only in a figure), one source at (3.5, 1.5, 1.5) whose Ricker band
     edge (2.5 f_peak) gives a shortest wavelength of 0.78 at c = 1, traces
     u(x, 0, 1.5) at every node x of the line, t in [0, 12.5].  The outer

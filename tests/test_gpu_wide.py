@@ -1,5 +1,5 @@
-"""Blocks wider than 64: the paper's own 25 cosine modes per face (5 x 5,
-b = 6m = 150; section "Numerical experiments") on the GPU.  The offline
+"""Blocks wider than 64: the paper's own 25 cosine modes per face
+(b = 6m = 150; section "Numerical experiments") on the GPU.  The offline
 builder (Algorithm 1 stage 1, Eqs. 5-13) and the FP64, two-float and FP32
 stepping (stage 2, Eqs. 12, 18, 19) against the oracle, and the modes that
 keep a block's tiles in one warp's registers refusing such blocks."""
@@ -31,7 +31,8 @@ def sfm():
 @pytest.fixture(scope="module")
 def wide():
     """2 x 2 x 1 subdomains of 8^3 cells (7 x 7 open-face nodes carry the
-    5 x 5 modes), m = 25 on every face, k = 3, random cell velocities."""
+    25 lowest cosine modes), m = 25 on every face, k = 3, random cell
+    velocities."""
     p = inputs.small_problem(ncell=(16, 16, 8), cuts=([0, 8, 16], [0, 8, 16], [0, 8]), m=25, k=3,
                              model="random",
                              rec=[[30.0, 40.0, 40.0], [120.0, 100.0, 40.0], [80.0, 80.0, 0.0]])
