@@ -53,3 +53,13 @@ def test_checkpoint_calls_reject_a_null_handle(lib):
     n = C.c_size_t(0)
     assert lib.sfm_checkpoint(None, None, C.byref(n)) == sfm.SFM_ERR_ARG
     assert lib.sfm_restore(None, None, 0) == sfm.SFM_ERR_ARG
+
+
+def test_read_probe_rejects_bad_arguments_before_any_device_call(lib):
+    import ctypes as C
+    from paper_1406_6923_gb300 import sfm
+    v = C.c_double(0.0)
+    assert lib.sfm_probe_read_gbs(0, 8, 4, C.byref(v)) == sfm.SFM_ERR_ARG       # fewer than 16 bytes
+    assert lib.sfm_probe_read_gbs(0, 1 << 20, 0, C.byref(v)) == sfm.SFM_ERR_ARG  # no repeat
+    assert lib.sfm_probe_read_gbs(0, 1 << 20, 4, None) == sfm.SFM_ERR_ARG        # no output
+    assert b"bad arguments" in lib.sfm_last_error(None)
